@@ -1,0 +1,143 @@
+/*
+ * bf.h -- C ABI of libbf: exhaustive low-spectrum search for Ising spin
+ * glasses on one NVIDIA GB300 (sm_103a).
+ *
+ * Problem (Jalowiecki, Rams, Gardas, "Brute-forcing spin-glass problems with
+ * CUDA", Sec. 2, Eq. (1), and Algorithm 1 of Sec. 3): for an Ising instance on
+ * n spins s_i in {-1, +1}, evaluate
+ *
+ *     E(s) = sum_{i<j} J_ij s_i s_j + sum_i h_i s_i
+ *
+ * for all 2^n configurations and return the S lowest (energy, configuration)
+ * pairs.  The paper's H of Eq. (1) carries an overall minus sign; negate J and
+ * h to obtain it.
+ *
+ * Conventions (fixed by this library where the paper is silent):
+ *   - Configuration integer (Sec. 3, Eqs. (4)-(5)): c = sum_i q_i 2^i with
+ *     q_i = (s_i + 1) / 2, i.e. bit i of c (least significant bit = spin 0)
+ *     is 1 iff s_i = +1.  n <= 64.
+ *   - J is a dense row-major n x n matrix; only its strict upper triangle
+ *     (i < j) is read.  The diagonal and lower triangle are ignored.
+ *   - Output order: ascending energy, ties broken by ascending c.  The result
+ *     is therefore unique.
+ *   - Integer instances (BF_I32) are exact.  Float instances (BF_F32, BF_F64)
+ *     are screened in exact fixed point with a rigorous quantisation bound and
+ *     every surviving candidate is re-evaluated in FP64; returned energies are
+ *     FP64 values of Eq. (1).
+ *
+ * Memory and streams: every pointer argument named "device" is device memory
+ * owned by the caller and must stay valid until the work queued on `stream`
+ * has completed.  The library never allocates device memory: the caller
+ * provides a workspace of at least bf_*_workspace_size() bytes, aligned to
+ * 256 bytes.  Calls on one workspace must not overlap in time.
+ *
+ * Errors: argument errors are detected on the host before anything is
+ * launched and reported by the return value.  Conditions found on the device
+ * (candidate storage exhausted) are recorded in the workspace and returned by
+ * bf_workspace_status(), which synchronises the stream.  On any error the
+ * outputs are undefined.  bf_last_error_detail() gives a per-thread message.
+ */
+#ifndef BF_H
+#define BF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BF_OK = 0,
+    BF_EINVAL = 1,        /* invalid argument (detected on the host) */
+    BF_ECUDA = 2,         /* a CUDA runtime call failed */
+    BF_EOVERFLOW = 3,     /* candidate storage in the workspace exhausted */
+    BF_ETIMEOUT = 4,      /* a bounded device-side wait gave up */
+    BF_EUNSUPPORTED = 5,  /* valid but outside what this build supports */
+    BF_EWORKSPACE = 6     /* workspace too small or misaligned */
+} bf_status;
+
+typedef enum {
+    BF_I32 = 0,  /* int32 couplings and fields; energies returned as int64 */
+    BF_F32 = 1,  /* float couplings and fields; energies returned as double */
+    BF_F64 = 2   /* double couplings and fields; energies returned as double */
+} bf_dtype;
+
+/* Screening kernel choice for bf_low_spectrum. */
+typedef enum {
+    BF_VARIANT_AUTO = 0,   /* library default (Gray-code walk) */
+    BF_VARIANT_GRAY = 1    /* Gray-code walk: exact int32 fixed point with a
+                              two-lane 16-bit pre-filter, one flip per step */
+} bf_variant;
+
+/*
+ * Options; a NULL pointer or zero fields select the defaults.
+ *   variant      one of bf_variant
+ *   fixed_bits   number of most significant configuration bits held fixed
+ *                (0 = enumerate all 2^n); the enumerated subspace is
+ *                c = (fixed_value << (n - fixed_bits)) + x, x in [0, 2^(n-fixed_bits)),
+ *                the paper's chunk offset of Sec. 3, Eq. (6)
+ *   fixed_value  value of those bits, < 2^fixed_bits
+ *   task_log2    log2 of the number of configurations one thread walks
+ *                per task (0 = automatic)
+ *   grid_blocks  persistent grid size of the enumeration kernel (0 = automatic)
+ */
+typedef struct {
+    int32_t variant;
+    int32_t fixed_bits;
+    uint64_t fixed_value;
+    int32_t task_log2;
+    int32_t grid_blocks;
+    int32_t reserved[8];
+} bf_options;
+
+/* Largest S accepted by bf_low_spectrum. */
+#define BF_MAX_S 2048
+
+/*
+ * Workspace bytes needed by bf_low_spectrum for (n, S, dtype, options).
+ * Returns 0 for arguments bf_low_spectrum would reject.
+ */
+size_t bf_workspace_size(int n, int S, bf_dtype dtype, const bf_options* opt);
+
+/*
+ * bf_low_spectrum -- the S lowest (energy, configuration) pairs of one
+ * instance (Algorithm 1, Sec. 3; energy of Eq. (1), Sec. 2).
+ *   J          device, n*n values of `dtype`, row-major; strict upper triangle read
+ *   h          device, n values of `dtype`
+ *   n          number of spins, 1 <= n <= 64; n - fixed_bits <= 62
+ *   S          number of states returned, 1 <= S <= min(BF_MAX_S, 2^(n-fixed_bits))
+ *   energies   device out, S values: int64 for BF_I32, double otherwise
+ *   states     device out, S configuration integers
+ *   workspace  device, >= bf_workspace_size(...) bytes, 256-byte aligned
+ *   stream     cudaStream_t (NULL = legacy default stream)
+ * Queues the whole search on `stream`.  The call blocks once, after a small
+ * preparation kernel, to copy its per-instance constants into the launch
+ * parameters of the enumeration kernel; it is therefore not capturable in a
+ * CUDA graph.  Returns BF_OK when the work was queued.
+ */
+bf_status bf_low_spectrum(const void* J, const void* h, int n, int S, bf_dtype dtype,
+                          void* energies, uint64_t* states,
+                          void* workspace, size_t workspace_bytes,
+                          const bf_options* opt, void* stream);
+
+/*
+ * Synchronises `stream` and returns the status recorded on the device by the
+ * last call that used `workspace` (BF_OK, BF_EOVERFLOW or BF_ETIMEOUT).
+ */
+bf_status bf_workspace_status(const void* workspace, void* stream);
+
+/* Human-readable name of a status code. */
+const char* bf_status_string(bf_status s);
+
+/* Detail of the last error raised on the calling host thread ("" if none). */
+const char* bf_last_error_detail(void);
+
+/* Library version string. */
+const char* bf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BF_H */

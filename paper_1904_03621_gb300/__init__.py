@@ -1,0 +1,22 @@
+"""GB300-native exhaustive low-spectrum search for Ising spin glasses.
+
+Imports are lazy: ``instances`` (seeded generators) can be used without
+loading the CUDA library; ``low_spectrum`` and friends load ``libbf.so`` on
+first use and raise if it is missing.
+"""
+import importlib
+
+__all__ = ["instances", "low_spectrum", "low_spectrum_batched", "low_spectrum_backward",
+           "LowSpectrumFn", "lib"]
+
+_API = ("low_spectrum", "low_spectrum_batched", "low_spectrum_backward", "LowSpectrumFn")
+
+
+def __getattr__(name):
+    if name == "instances":
+        return importlib.import_module(__name__ + ".instances")
+    if name == "lib":
+        return importlib.import_module(__name__ + "._lib")
+    if name in _API:
+        return getattr(importlib.import_module(__name__ + ".api"), name)
+    raise AttributeError(name)
