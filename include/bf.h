@@ -81,6 +81,9 @@ typedef enum {
  *   task_log2    log2 of the number of configurations one thread walks
  *                per task (0 = automatic)
  *   grid_blocks  persistent grid size of the enumeration kernel (0 = automatic)
+ *   spill_log2   log2 of the number of spill records in the workspace
+ *                (0 = default 21); a smaller area makes BF_EOVERFLOW reachable
+ *                in tests
  */
 typedef struct {
     int32_t variant;
@@ -88,7 +91,8 @@ typedef struct {
     uint64_t fixed_value;
     int32_t task_log2;
     int32_t grid_blocks;
-    int32_t reserved[8];
+    int32_t spill_log2;
+    int32_t reserved[7];
 } bf_options;
 
 /* Largest S accepted by bf_low_spectrum. */

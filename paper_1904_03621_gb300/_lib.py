@@ -1,0 +1,68 @@
+"""ctypes declarations of the C ABI in include/bf.h (argument marshalling only).
+
+Loading fails loudly when libbf.so has not been built: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libbf.so")
+
+BF_OK, BF_EINVAL, BF_ECUDA, BF_EOVERFLOW, BF_ETIMEOUT, BF_EUNSUPPORTED, BF_EWORKSPACE = range(7)
+BF_I32, BF_F32, BF_F64 = 0, 1, 2
+BF_VARIANT_AUTO, BF_VARIANT_GRAY = 0, 1
+
+# every symbol include/bf.h declares
+EXPORTS = ["bf_workspace_size", "bf_low_spectrum", "bf_workspace_status", "bf_status_string",
+           "bf_last_error_detail", "bf_version"]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("fixed_bits", ctypes.c_int32), ("fixed_value", ctypes.c_uint64),
+                ("task_log2", ctypes.c_int32), ("grid_blocks", ctypes.c_int32), ("spill_log2", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
+
+
+class BFError(RuntimeError):
+    def __init__(self, status: int, detail: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {detail}")
+        self.status = status
+
+
+STATUS_NAMES = {0: "BF_OK", 1: "BF_EINVAL", 2: "BF_ECUDA", 3: "BF_EOVERFLOW", 4: "BF_ETIMEOUT",
+                5: "BF_EUNSUPPORTED", 6: "BF_EWORKSPACE"}
+
+_lib = None
+
+
+def load(path: str | None = None):
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} not found: build the CUDA library first (paper_1904_03621_gb300.build.build())")
+    lib = ctypes.CDLL(p)
+    vp, sz, i32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int
+    lib.bf_workspace_size.restype = sz
+    lib.bf_workspace_size.argtypes = [i32, i32, i32, ctypes.POINTER(Options)]
+    lib.bf_low_spectrum.restype = i32
+    lib.bf_low_spectrum.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, sz, ctypes.POINTER(Options), vp]
+    lib.bf_workspace_status.restype = i32
+    lib.bf_workspace_status.argtypes = [vp, vp]
+    lib.bf_status_string.restype = ctypes.c_char_p
+    lib.bf_status_string.argtypes = [i32]
+    lib.bf_last_error_detail.restype = ctypes.c_char_p
+    lib.bf_last_error_detail.argtypes = []
+    lib.bf_version.restype = ctypes.c_char_p
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def check(status: int, lib=None):
+    if status != BF_OK:
+        lib = lib or load()
+        raise BFError(status, lib.bf_last_error_detail().decode())

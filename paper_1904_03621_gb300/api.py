@@ -1,0 +1,79 @@
+"""PyTorch-facing API: device memory, streams and argument marshalling only.
+
+Every step of the search runs in libbf's CUDA kernels; this module
+allocates the workspace and outputs with torch and passes raw pointers.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+
+_DTYPES = {torch.int32: _lib.BF_I32, torch.float32: _lib.BF_F32, torch.float64: _lib.BF_F64}
+
+
+def _stream_handle(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _options(variant=0, fixed_bits=0, fixed_value=0, task_log2=0, grid_blocks=0, spill_log2=0):
+    return _lib.Options(variant=variant, fixed_bits=fixed_bits, fixed_value=fixed_value,
+                        task_log2=task_log2, grid_blocks=grid_blocks, spill_log2=spill_log2)
+
+
+def workspace_size(n: int, S: int, dtype: torch.dtype, **opts) -> int:
+    lib = _lib.load()
+    o = _options(**opts)
+    nbytes = lib.bf_workspace_size(n, S, _DTYPES[dtype], ctypes.byref(o))
+    if nbytes == 0:
+        raise _lib.BFError(_lib.BF_EINVAL, lib.bf_last_error_detail().decode())
+    return int(nbytes)
+
+
+def low_spectrum(J: torch.Tensor, h: torch.Tensor, S: int, *, variant: int = 0, fixed_bits: int = 0,
+                 fixed_value: int = 0, task_log2: int = 0, grid_blocks: int = 0, spill_log2: int = 0, stream=None,
+                 workspace: torch.Tensor | None = None, check: bool = True):
+    """S lowest (energy, configuration) pairs of E(s) = sum_{i<j} J_ij s_i s_j + sum_i h_i s_i.
+
+    J: (n, n) CUDA tensor (int32, float32 or float64), strict upper triangle read.
+    h: (n,) CUDA tensor of the same dtype.
+    Returns (energies, states): energies int64 (int32 input) or float64, states as
+    int64 tensors holding the uint64 configuration integers (bit i = spin i is +1).
+    With check=True the stream is synchronised and device-side errors raise.
+    """
+    lib = _lib.load()
+    if J.dtype not in _DTYPES or h.dtype != J.dtype:
+        raise TypeError("J and h must share one of int32, float32, float64")
+    if not (J.is_cuda and h.is_cuda):
+        raise ValueError("J and h must be CUDA tensors")
+    n = J.shape[0]
+    J = J.contiguous()
+    h = h.contiguous()
+    o = _options(variant, fixed_bits, fixed_value, task_log2, grid_blocks, spill_log2)
+    nbytes = lib.bf_workspace_size(n, S, _DTYPES[J.dtype], ctypes.byref(o))
+    if nbytes == 0:
+        # the call validates its arguments before touching any pointer: get the exact status
+        _lib.check(lib.bf_low_spectrum(None, None, n, S, _DTYPES[J.dtype], None, None, None, 0,
+                                       ctypes.byref(o), None), lib)
+        raise _lib.BFError(_lib.BF_EINVAL, lib.bf_last_error_detail().decode())
+    if workspace is None or workspace.numel() < nbytes:
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device=J.device)
+    edt = torch.int64 if J.dtype == torch.int32 else torch.float64
+    energies = torch.empty(S, dtype=edt, device=J.device)
+    states = torch.empty(S, dtype=torch.int64, device=J.device)
+    sh = _stream_handle(stream)
+    st = lib.bf_low_spectrum(J.data_ptr(), h.data_ptr(), n, S, _DTYPES[J.dtype], energies.data_ptr(),
+                             states.data_ptr(), workspace.data_ptr(), workspace.numel(), ctypes.byref(o), sh)
+    _lib.check(st, lib)
+    if check:
+        _lib.check(lib.bf_workspace_status(workspace.data_ptr(), sh), lib)
+    return energies, states
+
+
+def states_u64(states: torch.Tensor) -> np.ndarray:
+    """Configuration integers as numpy uint64 (the int64 tensor holds their bits)."""
+    return states.detach().cpu().numpy().view(np.uint64)

@@ -1,0 +1,263 @@
+// Host side of the C ABI declared in include/bf.h: argument validation,
+// launch plan, workspace layout and the kernel sequence of one search.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "bf.h"
+#include "bf_internal.cuh"
+
+namespace {
+
+thread_local std::string g_detail;
+
+bf_status fail(bf_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_detail = buf;
+    return s;
+}
+
+bf_status cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(BF_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int ceil_log2(unsigned long long x)
+{
+    int k = 0;
+    while ((1ull << k) < x) k++;
+    return k;
+}
+
+struct Plan {
+    int n, S, dtype, free_bits;
+    unsigned long long hiconst;
+    bool direct;
+    int list_cap, grid, m, nh, seg_log2, seed_per_block, seed_blocks;
+    unsigned long long seed_sample;
+    bf::Layout L;
+    size_t bytes;
+};
+
+bf_status make_plan(int n, int S, int dtype, const bf_options* opt, Plan& pl)
+{
+    bf_options o{};
+    if (opt) o = *opt;
+    if (n < 1 || n > bf::kMaxN) return fail(BF_EINVAL, "n=%d outside [1, 64]", n);
+    if (dtype != BF_I32 && dtype != BF_F32 && dtype != BF_F64) return fail(BF_EINVAL, "unknown dtype %d", dtype);
+    if (o.variant != BF_VARIANT_AUTO && o.variant != BF_VARIANT_GRAY)
+        return fail(BF_EINVAL, "unknown variant %d", o.variant);
+    if (o.fixed_bits < 0 || o.fixed_bits > n) return fail(BF_EINVAL, "fixed_bits=%d outside [0, n]", o.fixed_bits);
+    const int free_bits = n - o.fixed_bits;
+    if (free_bits > 62) return fail(BF_EINVAL, "n - fixed_bits = %d > 62", free_bits);
+    if (o.fixed_bits < 64 && o.fixed_bits > 0 && (o.fixed_value >> o.fixed_bits) != 0)
+        return fail(BF_EINVAL, "fixed_value does not fit in fixed_bits=%d bits", o.fixed_bits);
+    if (o.fixed_bits == 0 && o.fixed_value != 0) return fail(BF_EINVAL, "fixed_value given without fixed_bits");
+    if (S < 1) return fail(BF_EINVAL, "S=%d < 1", S);
+    if ((unsigned long long)S > (1ull << free_bits)) return fail(BF_EINVAL, "S=%d exceeds 2^%d configurations", S, free_bits);
+    if (S > BF_MAX_S) return fail(BF_EUNSUPPORTED, "S=%d exceeds BF_MAX_S=%d", S, BF_MAX_S);
+    if (o.task_log2 < 0 || o.grid_blocks < 0) return fail(BF_EINVAL, "negative task_log2 or grid_blocks");
+    if (o.spill_log2 < 0 || o.spill_log2 > 28) return fail(BF_EINVAL, "spill_log2=%d outside [0, 28]", o.spill_log2);
+
+    pl = Plan{};
+    pl.n = n;
+    pl.S = S;
+    pl.dtype = dtype;
+    pl.free_bits = free_bits;
+    pl.hiconst = o.fixed_bits ? (o.fixed_value << free_bits) : 0ull;
+    pl.direct = free_bits <= bf::kSmallFreeBits;
+    if (pl.direct) {
+        pl.bytes = sizeof(bf::WsHeader);
+        return BF_OK;
+    }
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "device query");
+    pl.list_cap = bf::list_capacity(S);
+    int bps = bf::gray_blocks_per_sm(pl.list_cap);
+    if (bps < 1) return fail(BF_ECUDA, "enumeration kernel does not fit on an SM (S=%d)", S);
+    pl.grid = o.grid_blocks ? o.grid_blocks : sms * bps;
+    const int walk_bits = free_bits - bf::kInnerBits;    // middle + task-index bits
+    if (o.task_log2) {
+        pl.m = std::min(std::max(o.task_log2 - bf::kInnerBits, 0), walk_bits);
+    } else {
+        const int chains = ceil_log2((unsigned long long)pl.grid * bf::kGrayThreads * bf::kWalks);
+        pl.m = std::min(std::max(walk_bits - (chains + 2), 0), 14);
+    }
+    pl.nh = walk_bits - pl.m;
+    pl.seg_log2 = std::min(pl.m, 4);
+    // seed: a pseudo-random sample of up to 2^20 configurations, one sorted list per block
+    pl.seed_per_block = std::max(pl.list_cap, 2048);
+    unsigned long long sample = 1ull << std::min(free_bits, bf::kSeedLog2);
+    sample = std::min(sample, (unsigned long long)pl.grid * pl.seed_per_block);
+    pl.seed_sample = sample;
+    pl.seed_blocks = (int)((sample + pl.seed_per_block - 1) / pl.seed_per_block);
+    pl.L = bf::make_layout(S, pl.grid, o.spill_log2 ? o.spill_log2 : 21);
+    pl.bytes = pl.L.total;
+    return BF_OK;
+}
+
+// Pairwise merge rounds until one list is left; returns true if it is in A.
+cudaError_t merge_tree(int* AE, unsigned long long* AC, int* BE, unsigned long long* BC, int nin, int cap, int S,
+                       int W, bf::WsHeader* hdr, cudaStream_t stream, bool& in_a)
+{
+    in_a = true;
+    while (nin > 1) {
+        cudaError_t e = in_a ? bf::launch_merge_round(AE, AC, nin, BE, BC, cap, S, W, hdr, stream)
+                             : bf::launch_merge_round(BE, BC, nin, AE, AC, cap, S, W, hdr, stream);
+        if (e != cudaSuccess) return e;
+        nin = (nin + 1) / 2;
+        in_a = !in_a;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t bf_workspace_size(int n, int S, bf_dtype dtype, const bf_options* opt)
+{
+    Plan pl;
+    if (make_plan(n, S, dtype, opt, pl) != BF_OK) return 0;
+    return pl.bytes;
+}
+
+bf_status bf_low_spectrum(const void* J, const void* h, int n, int S, bf_dtype dtype, void* energies,
+                          uint64_t* states, void* workspace, size_t workspace_bytes, const bf_options* opt,
+                          void* stream_ptr)
+{
+    g_detail.clear();
+    Plan pl;
+    bf_status st = make_plan(n, S, dtype, opt, pl);
+    if (st != BF_OK) return st;
+    if (!J || !h || !energies || !states || !workspace) return fail(BF_EINVAL, "null pointer argument");
+    if (workspace_bytes < pl.bytes)
+        return fail(BF_EWORKSPACE, "workspace of %zu bytes < %zu required", workspace_bytes, pl.bytes);
+    if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return fail(BF_EWORKSPACE, "workspace not 256-byte aligned");
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    char* ws = static_cast<char*>(workspace);
+    auto* hdr = reinterpret_cast<bf::WsHeader*>(ws);
+    auto* out_states = reinterpret_cast<unsigned long long*>(states);
+
+    if (pl.direct) {
+        cudaError_t e = bf::launch_direct(J, h, n, dtype, S, pl.free_bits, pl.hiconst, energies, out_states, hdr, stream);
+        return e == cudaSuccess ? BF_OK : cuda_fail(e, "direct kernel");
+    }
+
+    const bf::Layout& L = pl.L;
+    auto* prep = reinterpret_cast<bf::Prep*>(ws + L.prep);
+    bf::PrepParams pp{};
+    pp.J = J;
+    pp.h = h;
+    pp.n = n;
+    pp.dtype = dtype;
+    pp.S = S;
+    pp.free_bits = pl.free_bits;
+    pp.hiconst = pl.hiconst;
+    pp.prep = prep;
+    pp.hdr = hdr;
+    cudaError_t e = bf::launch_prep(pp, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "prep kernel");
+
+    // The per-instance increments of the unrolled walk become kernel
+    // parameters (constant bank operands of the inner loop).
+    bf::PrepLaunch hl;
+    e = cudaMemcpyAsync(&hl, &prep->L, sizeof(hl), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e, "prep copy");
+    if (hl.status & bf::kErrRange)
+        return fail(BF_EUNSUPPORTED, "couplings outside the int32 fixed-point range (sum|J|+sum|h| = %g)", hl.emax);
+
+    int* AE = reinterpret_cast<int*>(ws + L.listA_E);
+    auto* AC = reinterpret_cast<unsigned long long*>(ws + L.listA_C);
+    int* BE = reinterpret_cast<int*>(ws + L.listB_E);
+    auto* BC = reinterpret_cast<unsigned long long*>(ws + L.listB_C);
+    bool in_a = true;
+
+    // seed threshold: S-th lowest quantised energy of a pseudo-random sample
+    e = bf::launch_seed(prep, n, pl.free_bits, pl.hiconst, pl.seed_sample, pl.seed_per_block, pl.seed_blocks,
+                        L.list_cap, AE, AC, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "seed kernel");
+    e = merge_tree(AE, AC, BE, BC, pl.seed_blocks, L.list_cap, S, 0, hdr, stream, in_a);
+    if (e != cudaSuccess) return cuda_fail(e, "seed merge");
+    e = bf::launch_set_tau(in_a ? AE : BE, S, hdr, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "seed threshold");
+
+    bf::GrayParams gp{};
+    std::memcpy(gp.dT16, hl.dT16, sizeof(gp.dT16));
+    gp.n = n;
+    gp.m = pl.m;
+    gp.nh = pl.nh;
+    gp.free_bits = pl.free_bits;
+    gp.hiconst = pl.hiconst;
+    gp.ntasks = 1ull << pl.nh;
+    gp.S = S;
+    gp.list_cap = L.list_cap;
+    gp.W = hl.W;
+    gp.seg_log2 = pl.seg_log2;
+    gp.spill_cap = L.spill_cap;
+    gp.prep = prep;
+    gp.hdr = hdr;
+    gp.list_E = AE;
+    gp.list_C = AC;
+    gp.spill_E = reinterpret_cast<int*>(ws + L.spill_E);
+    gp.spill_C = reinterpret_cast<unsigned long long*>(ws + L.spill_C);
+    e = bf::launch_gray(gp, pl.grid, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "enumeration kernel");
+
+    e = bf::launch_absorb_spill(AE, AC, pl.grid, L.list_cap, S, hl.W, gp.spill_E, gp.spill_C, L.spill_cap, hdr, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "spill absorb");
+    e = merge_tree(AE, AC, BE, BC, pl.grid, L.list_cap, S, hl.W, hdr, stream, in_a);
+    if (e != cudaSuccess) return cuda_fail(e, "merge rounds");
+    const int* FE = in_a ? AE : BE;
+    const unsigned long long* FC = in_a ? AC : BC;
+    e = bf::launch_finalize(FE, FC, L.list_cap, S, n, dtype, hl.q, J, h, reinterpret_cast<double*>(ws + L.rescore),
+                            energies, out_states, hdr, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "finalize");
+    return BF_OK;
+}
+
+bf_status bf_workspace_status(const void* workspace, void* stream_ptr)
+{
+    if (!workspace) return fail(BF_EINVAL, "null workspace");
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    unsigned status = 0;
+    const auto* hdr = static_cast<const bf::WsHeader*>(workspace);
+    cudaError_t e = cudaMemcpyAsync(&status, &hdr->status, sizeof(status), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e, "status copy");
+    if (status & (bf::kErrSpill | bf::kErrWindow))
+        return fail(BF_EOVERFLOW, "candidate storage exhausted (device status 0x%x)", status);
+    if (status & bf::kErrTimeout) return fail(BF_ETIMEOUT, "bounded device wait expired (device status 0x%x)", status);
+    if (status & bf::kErrRange) return fail(BF_EUNSUPPORTED, "instance outside the fixed-point range (0x%x)", status);
+    return BF_OK;
+}
+
+const char* bf_status_string(bf_status s)
+{
+    switch (s) {
+    case BF_OK: return "BF_OK";
+    case BF_EINVAL: return "BF_EINVAL";
+    case BF_ECUDA: return "BF_ECUDA";
+    case BF_EOVERFLOW: return "BF_EOVERFLOW";
+    case BF_ETIMEOUT: return "BF_ETIMEOUT";
+    case BF_EUNSUPPORTED: return "BF_EUNSUPPORTED";
+    case BF_EWORKSPACE: return "BF_EWORKSPACE";
+    }
+    return "BF_UNKNOWN";
+}
+
+const char* bf_last_error_detail(void) { return g_detail.c_str(); }
+
+const char* bf_version(void) { return "libbf 0.1 (sm_103a)"; }
+
+}  // extern "C"

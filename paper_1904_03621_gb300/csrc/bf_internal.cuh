@@ -1,0 +1,190 @@
+// Internal definitions shared by the libbf translation units.
+//
+// Numbers: an instance is screened in exact fixed point.  Couplings and
+// fields are scaled by 2^q and rounded to int32 (J_q, h_q) with q chosen so
+// that every energy and every local field of the quantised instance stays
+// below 2^29 in magnitude; all enumeration arithmetic on the quantised
+// instance is then exact in int32.  For integer instances the scaling is
+// exact.  For float instances the total rounding residual
+//     delta = sum_{i<j} |J_ij - J_q,ij 2^-q| + sum_i |h_i - h_q,i 2^-q|
+// bounds |E(c) - E_q(c) 2^-q| for every configuration c, so every member of
+// the exact top-S has E_q <= E_q,S + W with W = 2 delta 2^q (+ margin), and
+// the final answer is reselected from those candidates after an FP64
+// re-evaluation of Eq. (1).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bf {
+
+constexpr int kMaxN = 64;
+constexpr int kInnerBits = 8;                    // spins walked inside one unrolled block
+constexpr int kInnerSteps = 1 << kInnerBits;     // configurations per block and walk
+constexpr int kKeep = 4;                         // middle spins whose local field is kept in registers
+constexpr int kWalks = 4;                        // walks (tasks) per thread: two packed words
+constexpr int kGrayThreads = 256;                // block size of the enumeration kernel
+constexpr int kSmallFreeBits = 12;               // at most 2^12 configurations: direct kernel
+constexpr int kSeedLog2 = 20;                    // at most 2^20 sampled configurations for the seed
+constexpr int kMinListCap = 128;
+constexpr int kMaxListCap = 4096;
+constexpr int kEmqLog2 = 29;                     // |E_q|, |local field_q| < 2^29
+
+// Device status bits (workspace header).
+enum : unsigned {
+    kErrSpill = 1u,      // spill area exhausted: records were lost
+    kErrWindow = 2u,     // more near-ties than a list can hold
+    kErrTimeout = 4u,    // bounded wait gave up
+    kErrRange = 8u       // instance outside the supported fixed-point range
+};
+
+// Workspace header, first 256 bytes of the workspace.
+struct alignas(16) WsHeader {
+    int tau;                          // smallest known "S-th quantised energy" (upper bound of E_q,S)
+    unsigned status;                  // kErr* bits
+    unsigned long long task_next;     // dynamic task counter of the enumeration kernel
+    unsigned spill_count;             // records written to the spill area
+    unsigned pad0;
+    unsigned long long magic;         // set by every call, checked by bf_workspace_status
+    unsigned pad[56];
+};
+static_assert(sizeof(WsHeader) == 256, "header size");
+
+// Per-instance constants produced by the preparation kernel.  The leading
+// part (PrepLaunch) is copied to the host and becomes kernel parameters.
+struct PrepLaunch {
+    int status;           // kErr* bits found during preparation
+    int q;                // fixed-point scale exponent
+    int W;                // candidate window in quantised units (0 for integer instances)
+    int tau0;             // seed threshold (INT32 max if none)
+    double delta;         // quantisation residual bound (energy units)
+    double emax;          // sum |J| + sum |h| (energy units)
+    unsigned dT16[kInnerSteps];   // packed 16-bit pair-energy increments of the inner walk
+};
+
+struct Prep {
+    PrepLaunch L;
+    int Jq[kMaxN * kMaxN];        // quantised symmetric couplings, zero diagonal
+    int hq[kMaxN];
+    int T[kInnerSteps];           // exact inner pair energy T[g] (quantised units)
+    int colJ[kMaxN][16];          // column j: J_q[k][j] for k < 8, then J_q[8 + r][j] for r < 4
+};
+
+// Records: quantised energy (int32) + configuration (uint64), kept in two
+// arrays.  Order: (E, c) ascending.
+__host__ __device__ inline bool rec_less(int ea, unsigned long long ca, int eb, unsigned long long cb)
+{
+    return ea < eb || (ea == eb && ca < cb);
+}
+
+constexpr int kEmptyE = 0x7fffffff;
+constexpr unsigned long long kEmptyC = ~0ull;
+
+// Workspace layout of bf_low_spectrum.
+struct Layout {
+    size_t header, prep, listA_E, listA_C, listB_E, listB_C, spill_E, spill_C, rescore, total;
+    int lists, list_cap;
+    unsigned spill_cap;
+};
+
+__host__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+__host__ inline int next_pow2(int x)
+{
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+__host__ inline int list_capacity(int S)
+{
+    int c = next_pow2(2 * S);
+    if (c < kMinListCap) c = kMinListCap;
+    return c;
+}
+
+__host__ inline Layout make_layout(int S, int max_blocks, int spill_log2)
+{
+    Layout L{};
+    L.list_cap = list_capacity(S);
+    L.lists = max_blocks;
+    L.spill_cap = (unsigned)((size_t)1 << spill_log2);
+    size_t off = 0;
+    L.header = off;   off = align_up(off + sizeof(WsHeader), 256);
+    L.prep = off;     off = align_up(off + sizeof(Prep), 256);
+    size_t le = (size_t)L.lists * L.list_cap;
+    L.listA_E = off;  off = align_up(off + le * 4, 256);
+    L.listA_C = off;  off = align_up(off + le * 8, 256);
+    size_t lb = (size_t)((L.lists + 1) / 2) * L.list_cap;
+    L.listB_E = off;  off = align_up(off + lb * 4, 256);
+    L.listB_C = off;  off = align_up(off + lb * 8, 256);
+    L.spill_E = off;  off = align_up(off + (size_t)L.spill_cap * 4, 256);
+    L.spill_C = off;  off = align_up(off + (size_t)L.spill_cap * 8, 256);
+    L.rescore = off;  off = align_up(off + (size_t)L.list_cap * 8, 256);
+    L.total = off;
+    return L;
+}
+
+// ---- kernel parameter blocks -------------------------------------------
+
+struct GrayParams {
+    unsigned dT16[kInnerSteps];     // index t = 1..255; entry 0 unused
+    int n, m, nh;                   // spins, walked middle spins, task-index bits
+    int free_bits;
+    unsigned long long hiconst;     // fixed top bits of every configuration
+    unsigned long long ntasks;      // 2^nh
+    int S, list_cap, W, seg_log2;
+    unsigned spill_cap;
+    int pad0;
+    const Prep* prep;
+    WsHeader* hdr;
+    int* list_E;
+    unsigned long long* list_C;
+    int* spill_E;
+    unsigned long long* spill_C;
+};
+
+struct PrepParams {
+    const void* J;
+    const void* h;
+    int n, dtype, S, free_bits;
+    unsigned long long hiconst;
+    int seed_count;
+    int pad0;
+    Prep* prep;
+    WsHeader* hdr;
+};
+
+// ---- launchers (defined in the .cu files) ----------------------------
+
+cudaError_t launch_prep(const PrepParams& p, cudaStream_t s);
+cudaError_t launch_gray(const GrayParams& p, int grid, cudaStream_t s);
+int gray_blocks_per_sm(int list_cap);
+size_t gray_smem_bytes(int n, int list_cap);
+
+// Merge of sorted record lists: `nin` lists of `cap` records each in
+// (inE, inC) are merged pairwise into ceil(nin / 2) lists in (outE, outC).
+cudaError_t launch_merge_round(const int* inE, const unsigned long long* inC, int nin,
+                               int* outE, unsigned long long* outC, int cap, int S, int W,
+                               WsHeader* hdr, cudaStream_t s);
+// Fold the spill area into the `nlists` lists of (E, C) (grid-stride over chunks).
+cudaError_t launch_absorb_spill(int* E, unsigned long long* C, int nlists, int cap, int S, int W,
+                                const int* spill_E, const unsigned long long* spill_C,
+                                unsigned spill_cap, WsHeader* hdr, cudaStream_t s);
+// Final selection: integer instances write E_q >> q; float instances
+// re-evaluate Eq. (1) in FP64 from the caller's J, h and reselect.
+cudaError_t launch_finalize(const int* E, const unsigned long long* C, int cap, int S, int n, int dtype,
+                            int q, const void* J, const void* h, double* rescore,
+                            void* energies, unsigned long long* states, WsHeader* hdr, cudaStream_t s);
+// Seed: `blocks` lists of the lowest sampled records (sample configurations in total).
+cudaError_t launch_seed(const Prep* prep, int n, int free_bits, unsigned long long hiconst,
+                        unsigned long long sample, int per_block, int blocks, int cap, int* outE,
+                        unsigned long long* outC, cudaStream_t s);
+// hdr->tau = E[S - 1] of a merged list; resets the task and spill counters.
+cudaError_t launch_set_tau(const int* E, int S, WsHeader* hdr, cudaStream_t s);
+// Small instances (<= 2^kSmallFreeBits configurations): direct enumeration.
+cudaError_t launch_direct(const void* J, const void* h, int n, int dtype, int S, int free_bits,
+                          unsigned long long hiconst, void* energies, unsigned long long* states,
+                          WsHeader* hdr, cudaStream_t s);
+
+}  // namespace bf

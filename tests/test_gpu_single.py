@@ -1,0 +1,229 @@
+"""bf_low_spectrum on the GPU against the oracle (single instance)."""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from parity import assert_float_parity, assert_int_equal
+from paper_1904_03621_gb300 import instances
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module")
+def bf():
+    import torch
+    from paper_1904_03621_gb300 import build
+    build.build()
+    from paper_1904_03621_gb300 import api
+    assert torch.cuda.is_available()
+    return api
+
+
+@pytest.fixture(scope="module")
+def o():
+    return oracle.get()
+
+
+def run(bf, J, h, S, **kw):
+    import torch
+    Jt = torch.as_tensor(np.ascontiguousarray(J)).cuda()
+    ht = torch.as_tensor(np.ascontiguousarray(h)).cuda()
+    en, st = bf.low_spectrum(Jt, ht, S, **kw)
+    return en.cpu().numpy(), bf.states_u64(st)
+
+
+def check(bf, o, J, h, S, **kw):
+    en, st = run(bf, J, h, S, **kw)
+    fb, fv = kw.get("fixed_bits", 0), kw.get("fixed_value", 0)
+    n = np.asarray(J).shape[0]
+    if np.issubdtype(np.asarray(J).dtype, np.integer):
+        en_o, st_o = o.low_spectrum(J, h, S, fixed_bits=fb, fixed_value=fv)
+        assert_int_equal(en, st, en_o, st_o)
+    else:
+        S1 = min(S + 1, 1 << (n - fb))
+        Jd = np.asarray(J, dtype=np.float64)
+        hd = np.asarray(h, dtype=np.float64)
+        en_o, st_o = o.low_spectrum(Jd, hd, S1, fixed_bits=fb, fixed_value=fv)
+        assert_float_parity(o, Jd, hd, en, st, en_o, st_o)
+    return en, st
+
+
+def rand_float(n, seed, dtype=np.float64, h_std=1.0):
+    J, h = instances.dense_gaussian(n, seed, h_std=h_std)
+    return J.astype(dtype), h.astype(dtype)
+
+
+def rand_pm1(n, seed):
+    return instances.dense_pm1(n, seed)
+
+
+# ---- small search spaces (direct kernel) -----------------------------------
+
+@pytest.mark.parametrize("n,S", [(1, 1), (1, 2), (2, 4), (5, 7), (9, 512), (12, 100), (12, 2048)])
+def test_direct_float(bf, o, n, S):
+    J, h = rand_float(n, 100 + n)
+    check(bf, o, J, h, S)
+
+
+@pytest.mark.parametrize("n,S", [(3, 8), (10, 1), (12, 1000)])
+def test_direct_int(bf, o, n, S):
+    J, h = rand_pm1(n, 200 + n)
+    check(bf, o, J, h, S)
+
+
+def test_paper_example(bf, o):
+    J = np.array([[0.0, -0.2], [0.0, 0.0]])
+    h = np.array([-1.0, 0.0])
+    en, st = run(bf, J, h, 4)
+    assert list(st) == [3, 1, 0, 2]
+    assert np.allclose(en, [-1.2, -0.8, 0.8, 1.2], atol=1e-12)
+
+
+# ---- Gray-code path ------------------------------------------------------------
+
+@pytest.mark.parametrize("n,S,seed", [(13, 1, 0), (13, 10, 1), (14, 100, 2), (16, 1000, 3), (18, 2048, 4),
+                                      (20, 10, 0), (22, 100, 5), (24, 1000, 6)])
+def test_gray_float64(bf, o, n, S, seed):
+    J, h = rand_float(n, seed)
+    check(bf, o, J, h, S)
+
+
+@pytest.mark.parametrize("n,S,seed", [(16, 32, 7), (20, 100, 8)])
+def test_gray_float32(bf, o, n, S, seed):
+    J, h = rand_float(n, seed, dtype=np.float32)
+    check(bf, o, J, h, S)
+
+
+@pytest.mark.parametrize("n,S,seed", [(13, 5, 0), (16, 17, 1), (20, 100, 2), (23, 2048, 3), (24, 100, 4)])
+def test_gray_int_pm1(bf, o, n, S, seed):
+    J, h = rand_pm1(n, seed)
+    check(bf, o, J, h, S)
+
+
+def test_gray_int_wide_range(bf, o):
+    rng = np.random.default_rng(21)
+    n = 20
+    U = rng.integers(-100000, 100000, (n, n))
+    J = np.triu(U, 1)
+    J = (J + J.T).astype(np.int32)
+    h = rng.integers(-50000, 50000, n).astype(np.int32)
+    check(bf, o, J, h, 50)
+
+
+def test_plain_n20(bf, o):
+    J, h = instances.plain_n20()
+    check(bf, o, J, h, 10)
+
+
+def test_ferromagnet(bf, o):
+    for dt in (np.int32, np.float64):
+        J, h = instances.ferromagnet(20, dtype=dt)
+        check(bf, o, J, h, 100)
+
+
+def test_all_degenerate_ties(bf, o):
+    """J = 0, h = 0: every configuration is a hit; forces the spill path."""
+    n = 18
+    for dt in (np.int32, np.float64):
+        J = np.zeros((n, n), dtype=dt)
+        h = np.zeros(n, dtype=dt)
+        en, st = run(bf, J, h, 100)
+        assert list(st) == list(range(100)) and np.all(en == 0)
+
+
+def test_subspace_fixed_bits(bf, o):
+    J, h = rand_float(30, 31)
+    for v in (0, 77, 1023):
+        check(bf, o, J, h, 50, fixed_bits=10, fixed_value=v)
+
+
+def test_n64_subspace(bf, o):
+    J, h = rand_float(64, 64)
+    check(bf, o, J, h, 20, fixed_bits=44, fixed_value=(1 << 44) - 12345)
+    Ji, hi = rand_pm1(64, 64)
+    check(bf, o, Ji, hi, 20, fixed_bits=45, fixed_value=987654321)
+
+
+def test_task_and_grid_options(bf, o):
+    J, h = rand_float(22, 41)
+    ref = None
+    for kw in ({}, {"task_log2": 8}, {"task_log2": 12, "grid_blocks": 3}, {"grid_blocks": 1}):
+        en, st = check(bf, o, J, h, 64, **kw)
+        if ref is None:
+            ref = (en, st)
+        assert np.array_equal(st, ref[1])
+
+
+def test_invalid_arguments(bf):
+    import torch
+    from paper_1904_03621_gb300 import _lib
+    J = torch.zeros(4, 4, dtype=torch.float64, device="cuda")
+    h = torch.zeros(4, dtype=torch.float64, device="cuda")
+    with pytest.raises(_lib.BFError) as e:
+        bf.low_spectrum(J, h, 17)
+    assert e.value.status == _lib.BF_EINVAL
+    J = torch.zeros(20, 20, dtype=torch.float64, device="cuda")
+    h = torch.zeros(20, dtype=torch.float64, device="cuda")
+    with pytest.raises(_lib.BFError) as e:
+        bf.low_spectrum(J, h, 4096)
+    assert e.value.status == _lib.BF_EUNSUPPORTED
+    ws = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    lib = _lib.load()
+    en = torch.empty(10, dtype=torch.float64, device="cuda")
+    st = torch.empty(10, dtype=torch.int64, device="cuda")
+    import ctypes
+    s = lib.bf_low_spectrum(J.data_ptr(), h.data_ptr(), 20, 10, _lib.BF_F64, en.data_ptr(), st.data_ptr(),
+                            ws.data_ptr(), 1024, None, None)
+    assert s == _lib.BF_EWORKSPACE
+
+
+def test_spill_overflow_reports_status(bf):
+    """A flood of equal energies into a 16-record spill area must report BF_EOVERFLOW,
+    and the same call with the default area must succeed."""
+    import torch
+    from paper_1904_03621_gb300 import _lib
+    n = 20
+    J = torch.zeros(n, n, dtype=torch.float64, device="cuda")
+    h = torch.zeros(n, dtype=torch.float64, device="cuda")
+    with pytest.raises(_lib.BFError) as e:
+        bf.low_spectrum(J, h, 10, spill_log2=4)
+    assert e.value.status == _lib.BF_EOVERFLOW
+    en, st = bf.low_spectrum(J, h, 10)
+    assert bf.states_u64(st).tolist() == list(range(10))
+
+
+# ---- full-size workloads against stored oracle results -------------------------
+
+def _golden(name):
+    import importlib.util
+    path = os.path.join(GOLDEN, name)
+    if not os.path.exists(path):
+        pytest.skip(f"{name} not generated")
+    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(GOLDEN, "make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    return mg, mg.read(path)
+
+
+def test_int_n32_full(bf):
+    """n = 32, J uniform in {-1, +1}, h = 0, S = 100: bit-exact against the full oracle enumeration."""
+    _, gold = _golden("int_n32_S100.txt.gz")
+    J, h = instances.int_n32()
+    en, st = run(bf, J, h, 100)
+    assert_int_equal(en, st, gold[0][0], gold[0][1])
+
+
+def test_float_n48_subspaces(bf, o):
+    """n = 48 float instance on 64 fixed-prefix subspaces (top 24 bits fixed), S = 1000."""
+    mg, gold = _golden("float_n48_sub24_S1000.txt.gz")
+    J, h = instances.float_n48()
+    for v, (en_o, st_o) in sorted(gold.items()):
+        en, st = run(bf, J, h, mg.N48_S, fixed_bits=mg.N48_FIXED_BITS, fixed_value=v)
+        # stored records have S entries: parity without the (S+1)-th gap check
+        assert_float_parity(o, J, h, en, st, en_o, st_o)
