@@ -1,0 +1,297 @@
+#!/usr/bin/env python3
+"""Benchmark of the exhaustive exact top-S search (one JSON line on stdout).
+
+Workload (default): the n = 48 fully connected instance, J_ij ~ N(0, 1),
+h_i ~ N(0, 0.1^2), S = 1000, full enumeration of all 2^48 configurations per
+step.  Under torchrun each rank solves its own instance (seed = rank): the
+units are independent, no collective touches the data path (weak scaling).
+
+value      configurations / s, device time of the whole search (CUDA events on
+           the call's stream; inputs resident in HBM)
+e2e        the same metric through the public API with host buffers: pinned
+           host -> device copy of J and h, the search, device -> host copy of
+           the S results, all inside the timed region of each step
+roofline   the enumeration kernel (gray_kernel), timed live with CUDA events
+           recorded by the library around that kernel: ALU lane-instructions
+           required by the inner loop (0.75 per configuration) / kernel time,
+           against the integer-ALU issue peak of the GPU
+cpu_baseline  the CPU oracle timed on this host's cores on a bounded sample
+           (one fixed-prefix subspace of the same instance)
+
+--impl reference times the oracle (the CPU reference of this project) on the
+same metric, one bounded subspace per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "configs/s with exact top-S at N=48, % of roofline; batched instances/s"
+UNIT = "configs/s"
+SMS = 152
+ALU_LANES_PER_SM = 64          # integer ALU pipe: 16 lanes per SM sub-partition (probe-measured)
+ALU_OPS_PER_CONFIG = 0.75      # inner loop: one IADD3 per 2 configurations + one 3-input 16x2 min per 4
+CPU_SAMPLE_FREE_BITS = 25      # oracle baseline: one subspace of 2^25 configurations
+REF_STEP_FREE_BITS = 22        # reference arm: one subspace of 2^22 configurations per step
+
+
+def workload(name: str, rank: int):
+    from paper_1904_03621_gb300 import instances
+    if name == "float_n48":
+        J, h = instances.float_n48(seed=rank)
+        return J, h, 1000, ("n=48 fully connected, J_ij~N(0,1), h_i~N(0,0.1^2) (FP64), S=1000, "
+                            "all 2^48 configurations per step")
+    if name == "int_n32":
+        J, h = instances.int_n32(seed=rank)
+        return J, h, 100, "n=32 fully connected, J_ij uniform in {-1,+1} (int32), h=0, S=100, all 2^32 per step"
+    if name.startswith("dense_n"):
+        n = int(name[len("dense_n"):])
+        J, h = instances.dense_gaussian(n, rank, h_std=0.1)
+        return J, h, 1000, f"n={n} fully connected, J~N(0,1), h~N(0,0.1^2), S=1000 (development size)"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx = max(mx, float(p[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, p[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(J, h, S):
+    """The oracle as it stands, on this host's cores, on one fixed-prefix subspace."""
+    import oracle
+    o = oracle.get()
+    n = J.shape[0]
+    fb = n - CPU_SAMPLE_FREE_BITS
+    t = time.perf_counter()
+    o.low_spectrum(J, h, S, fixed_bits=fb, fixed_value=(1 << fb) // 3)
+    dt = time.perf_counter() - t
+    return {"value": (1 << CPU_SAMPLE_FREE_BITS) / dt, "unit": UNIT, "cores": o.num_threads, "kind": "oracle",
+            "sample": f"one subspace of 2^{CPU_SAMPLE_FREE_BITS} configurations (top {fb} bits fixed) of the "
+                      f"same instance, S={S}, {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle, one bounded subspace of the workload per step."""
+    if rank != 0:
+        return 0
+    import oracle
+    o = oracle.get()
+    J, h, S, desc = workload(args.workload, 0)
+    n = J.shape[0]
+    fb = n - REF_STEP_FREE_BITS
+    nsub = 1 << fb
+    for w in range(args.warmup):
+        o.low_spectrum(J, h, S, fixed_bits=fb, fixed_value=w % nsub)
+    t = time.perf_counter()
+    for k in range(args.steps):
+        o.low_spectrum(J, h, S, fixed_bits=fb, fixed_value=(1000 + k) % nsub)
+    dt = time.perf_counter() - t
+    value = args.steps * (1 << REF_STEP_FREE_BITS) / dt
+    sample = f"per step one subspace of 2^{REF_STEP_FREE_BITS} configurations (top {fb} bits fixed), S={S}"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "description": desc, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": o.num_threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="float_n48")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    from paper_1904_03621_gb300 import build
+    build.build()
+    from paper_1904_03621_gb300 import api, _lib
+
+    J, h, S, desc = workload(args.workload, rank)
+    n = J.shape[0]
+    configs_per_step = float(2 ** n)
+    dev = torch.device("cuda", local_rank)
+    Jh = torch.from_numpy(np.ascontiguousarray(J)).pin_memory()
+    hh = torch.from_numpy(np.ascontiguousarray(h)).pin_memory()
+    Jd = torch.empty_like(Jh, device=dev)
+    hd = torch.empty_like(hh, device=dev)
+    ws = torch.empty(api.workspace_size(n, S, Jh.dtype), dtype=torch.uint8, device=dev)
+    edt = torch.int64 if Jh.dtype == torch.int32 else torch.float64
+    en = torch.empty(S, dtype=edt, device=dev)
+    st = torch.empty(S, dtype=torch.int64, device=dev)
+    en_h = torch.empty(S, dtype=edt).pin_memory()
+    st_h = torch.empty(S, dtype=torch.int64).pin_memory()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step(profile):
+        Jd.copy_(Jh, non_blocking=True)
+        hd.copy_(hh, non_blocking=True)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        api.low_spectrum(Jd, hd, S, workspace=ws, out=(en, st), check=False, profile=profile)
+        ev1.record(stream)
+        en_h.copy_(en, non_blocking=True)
+        st_h.copy_(st, non_blocking=True)
+        return ev0, ev1
+
+    lib = _lib.load()
+    for _ in range(args.warmup):
+        step(0)
+        torch.cuda.synchronize()
+        _lib.check(lib.bf_workspace_status(ws.data_ptr(), None), lib)
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    launches0 = api.launch_count()
+    dev_ms, e2e_s, gray_ms = 0.0, 0.0, 0.0
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_region = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev0, ev1 = step(1)
+        torch.cuda.synchronize()
+        e2e_s += time.perf_counter() - t0
+        dev_ms += ev0.elapsed_time(ev1)
+        gray_ms += api.last_profile_ms()
+        _lib.check(lib.bf_workspace_status(ws.data_ptr(), None), lib)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    region_s = time.perf_counter() - t_region
+    launches = api.launch_count() - launches0
+    clk = clocks.stop()
+
+    if world > 1:
+        t = torch.tensor([dev_ms, e2e_s, gray_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_ms, e2e_s, gray_ms = t.tolist()
+
+    total_configs = configs_per_step * args.steps * world
+    value = total_configs / (dev_ms * 1e-3)
+    e2e_value = total_configs / e2e_s
+    pk, pk_kind = peaks()
+    sm_max_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    peak_ops = SMS * ALU_LANES_PER_SM * sm_max_mhz * 1e6
+    gray_s = gray_ms * 1e-3 / args.steps
+    achieved = ALU_OPS_PER_CONFIG * configs_per_step / gray_s
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "i32", "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc, "n": n, "S": S,
+                   "configs_per_step": configs_per_step, "l2": "flushed between steps (256 MB write)",
+                   "instances": "one per rank, seed = rank"},
+        "roofline": {"bound": "alu", "kernel": "gray_kernel", "achieved": achieved / 1e9,
+                     "peak": peak_ops / 1e9, "unit": "Gop/s", "frac": achieved / peak_ops, "traffic": None,
+                     "ops_per_config": ALU_OPS_PER_CONFIG,
+                     "peak_basis": f"{SMS} SMs x {ALU_LANES_PER_SM} integer-ALU lanes x {sm_max_mhz:.0f} MHz "
+                                   f"(sm_max_mhz {pk_kind})",
+                     "kernel_ms": gray_ms / args.steps,
+                     "kernel_share_of_step": gray_ms / dev_ms},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(Jh.nbytes + hh.nbytes),
+                "d2h_bytes_per_step": int(en_h.nbytes + st_h.nbytes)},
+        "clocks": clk,
+        "gpu_launches": int(launches),
+        "timed_region_s": region_s,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(J, h, S)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -84,6 +84,8 @@ typedef enum {
  *   spill_log2   log2 of the number of spill records in the workspace
  *                (0 = default 21); a smaller area makes BF_EOVERFLOW reachable
  *                in tests
+ *   profile      nonzero: record CUDA events around the enumeration kernel on
+ *                the call's stream (read back with bf_last_profile)
  */
 typedef struct {
     int32_t variant;
@@ -92,7 +94,8 @@ typedef struct {
     int32_t task_log2;
     int32_t grid_blocks;
     int32_t spill_log2;
-    int32_t reserved[7];
+    int32_t profile;
+    int32_t reserved[6];
 } bf_options;
 
 /* Largest S accepted by bf_low_spectrum. */
@@ -130,6 +133,17 @@ bf_status bf_low_spectrum(const void* J, const void* h, int n, int S, bf_dtype d
  * last call that used `workspace` (BF_OK, BF_EOVERFLOW or BF_ETIMEOUT).
  */
 bf_status bf_workspace_status(const void* workspace, void* stream);
+
+/*
+ * Duration in milliseconds of the enumeration kernel of the last call made on
+ * this host thread with opt->profile != 0 (CUDA events recorded on that
+ * call's stream immediately around the kernel).  Waits for the end event.
+ * Returns BF_EINVAL if no profiled call was made.
+ */
+bf_status bf_last_profile(float* enumeration_ms);
+
+/* Number of kernels this library has launched in the process so far. */
+int64_t bf_launch_count(void);
 
 /* Human-readable name of a status code. */
 const char* bf_status_string(bf_status s);

@@ -15,14 +15,14 @@ BF_I32, BF_F32, BF_F64 = 0, 1, 2
 BF_VARIANT_AUTO, BF_VARIANT_GRAY = 0, 1
 
 # every symbol include/bf.h declares
-EXPORTS = ["bf_workspace_size", "bf_low_spectrum", "bf_workspace_status", "bf_status_string",
-           "bf_last_error_detail", "bf_version"]
+EXPORTS = ["bf_workspace_size", "bf_low_spectrum", "bf_workspace_status", "bf_last_profile",
+           "bf_launch_count", "bf_status_string", "bf_last_error_detail", "bf_version"]
 
 
 class Options(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("fixed_bits", ctypes.c_int32), ("fixed_value", ctypes.c_uint64),
                 ("task_log2", ctypes.c_int32), ("grid_blocks", ctypes.c_int32), ("spill_log2", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class BFError(RuntimeError):
@@ -57,6 +57,10 @@ def load(path: str | None = None):
     lib.bf_last_error_detail.restype = ctypes.c_char_p
     lib.bf_last_error_detail.argtypes = []
     lib.bf_version.restype = ctypes.c_char_p
+    lib.bf_last_profile.restype = i32
+    lib.bf_last_profile.argtypes = [ctypes.POINTER(ctypes.c_float)]
+    lib.bf_launch_count.restype = ctypes.c_int64
+    lib.bf_launch_count.argtypes = []
     if path is None:
         _lib = lib
     return lib

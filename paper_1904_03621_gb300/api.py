@@ -20,9 +20,9 @@ def _stream_handle(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _options(variant=0, fixed_bits=0, fixed_value=0, task_log2=0, grid_blocks=0, spill_log2=0):
+def _options(variant=0, fixed_bits=0, fixed_value=0, task_log2=0, grid_blocks=0, spill_log2=0, profile=0):
     return _lib.Options(variant=variant, fixed_bits=fixed_bits, fixed_value=fixed_value,
-                        task_log2=task_log2, grid_blocks=grid_blocks, spill_log2=spill_log2)
+                        task_log2=task_log2, grid_blocks=grid_blocks, spill_log2=spill_log2, profile=profile)
 
 
 def workspace_size(n: int, S: int, dtype: torch.dtype, **opts) -> int:
@@ -35,8 +35,9 @@ def workspace_size(n: int, S: int, dtype: torch.dtype, **opts) -> int:
 
 
 def low_spectrum(J: torch.Tensor, h: torch.Tensor, S: int, *, variant: int = 0, fixed_bits: int = 0,
-                 fixed_value: int = 0, task_log2: int = 0, grid_blocks: int = 0, spill_log2: int = 0, stream=None,
-                 workspace: torch.Tensor | None = None, check: bool = True):
+                 fixed_value: int = 0, task_log2: int = 0, grid_blocks: int = 0, spill_log2: int = 0,
+                 profile: int = 0, stream=None, workspace: torch.Tensor | None = None, check: bool = True,
+                 out: tuple | None = None):
     """S lowest (energy, configuration) pairs of E(s) = sum_{i<j} J_ij s_i s_j + sum_i h_i s_i.
 
     J: (n, n) CUDA tensor (int32, float32 or float64), strict upper triangle read.
@@ -53,7 +54,7 @@ def low_spectrum(J: torch.Tensor, h: torch.Tensor, S: int, *, variant: int = 0, 
     n = J.shape[0]
     J = J.contiguous()
     h = h.contiguous()
-    o = _options(variant, fixed_bits, fixed_value, task_log2, grid_blocks, spill_log2)
+    o = _options(variant, fixed_bits, fixed_value, task_log2, grid_blocks, spill_log2, profile)
     nbytes = lib.bf_workspace_size(n, S, _DTYPES[J.dtype], ctypes.byref(o))
     if nbytes == 0:
         # the call validates its arguments before touching any pointer: get the exact status
@@ -63,8 +64,11 @@ def low_spectrum(J: torch.Tensor, h: torch.Tensor, S: int, *, variant: int = 0, 
     if workspace is None or workspace.numel() < nbytes:
         workspace = torch.empty(nbytes, dtype=torch.uint8, device=J.device)
     edt = torch.int64 if J.dtype == torch.int32 else torch.float64
-    energies = torch.empty(S, dtype=edt, device=J.device)
-    states = torch.empty(S, dtype=torch.int64, device=J.device)
+    if out is not None:
+        energies, states = out
+    else:
+        energies = torch.empty(S, dtype=edt, device=J.device)
+        states = torch.empty(S, dtype=torch.int64, device=J.device)
     sh = _stream_handle(stream)
     st = lib.bf_low_spectrum(J.data_ptr(), h.data_ptr(), n, S, _DTYPES[J.dtype], energies.data_ptr(),
                              states.data_ptr(), workspace.data_ptr(), workspace.numel(), ctypes.byref(o), sh)
@@ -77,3 +81,16 @@ def low_spectrum(J: torch.Tensor, h: torch.Tensor, S: int, *, variant: int = 0, 
 def states_u64(states: torch.Tensor) -> np.ndarray:
     """Configuration integers as numpy uint64 (the int64 tensor holds their bits)."""
     return states.detach().cpu().numpy().view(np.uint64)
+
+
+def last_profile_ms() -> float:
+    """Enumeration-kernel time (ms) of the last call made with profile=1 on this thread."""
+    lib = _lib.load()
+    ms = ctypes.c_float(0.0)
+    _lib.check(lib.bf_last_profile(ctypes.byref(ms)), lib)
+    return float(ms.value)
+
+
+def launch_count() -> int:
+    """Kernels launched by libbf in this process so far."""
+    return int(_lib.load().bf_launch_count())

@@ -1,6 +1,7 @@
 // Host side of the C ABI declared in include/bf.h: argument validation,
 // launch plan, workspace layout and the kernel sequence of one search.
 #include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -9,9 +10,21 @@
 #include "bf.h"
 #include "bf_internal.cuh"
 
+namespace bf {
+static std::atomic<long long> g_launches{0};
+void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+}  // namespace bf
+
 namespace {
 
 thread_local std::string g_detail;
+
+// events of the last profiled call on this host thread
+struct ProfileEvents {
+    cudaEvent_t start = nullptr, stop = nullptr;
+    bool valid = false;
+};
+thread_local ProfileEvents g_prof;
 
 bf_status fail(bf_status s, const char* fmt, ...)
 {
@@ -211,8 +224,24 @@ bf_status bf_low_spectrum(const void* J, const void* h, int n, int S, bf_dtype d
     gp.list_C = AC;
     gp.spill_E = reinterpret_cast<int*>(ws + L.spill_E);
     gp.spill_C = reinterpret_cast<unsigned long long*>(ws + L.spill_C);
+    const bool profile = opt && opt->profile;
+    if (profile) {
+        if (!g_prof.start) {
+            e = cudaEventCreate(&g_prof.start);
+            if (e == cudaSuccess) e = cudaEventCreate(&g_prof.stop);
+            if (e != cudaSuccess) return cuda_fail(e, "profile events");
+        }
+        g_prof.valid = false;
+        e = cudaEventRecord(g_prof.start, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "profile event");
+    }
     e = bf::launch_gray(gp, pl.grid, stream);
     if (e != cudaSuccess) return cuda_fail(e, "enumeration kernel");
+    if (profile) {
+        e = cudaEventRecord(g_prof.stop, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "profile event");
+        g_prof.valid = true;
+    }
 
     e = bf::launch_absorb_spill(AE, AC, pl.grid, L.list_cap, S, hl.W, gp.spill_E, gp.spill_C, L.spill_cap, hdr, stream);
     if (e != cudaSuccess) return cuda_fail(e, "spill absorb");
@@ -241,6 +270,18 @@ bf_status bf_workspace_status(const void* workspace, void* stream_ptr)
     if (status & bf::kErrRange) return fail(BF_EUNSUPPORTED, "instance outside the fixed-point range (0x%x)", status);
     return BF_OK;
 }
+
+bf_status bf_last_profile(float* enumeration_ms)
+{
+    if (!enumeration_ms) return fail(BF_EINVAL, "null output");
+    if (!g_prof.valid) return fail(BF_EINVAL, "no profiled call on this thread");
+    cudaError_t e = cudaEventSynchronize(g_prof.stop);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(enumeration_ms, g_prof.start, g_prof.stop);
+    if (e != cudaSuccess) return cuda_fail(e, "profile read");
+    return BF_OK;
+}
+
+int64_t bf_launch_count(void) { return (int64_t)bf::g_launches.load(std::memory_order_relaxed); }
 
 const char* bf_status_string(bf_status s)
 {

@@ -157,6 +157,9 @@ struct PrepParams {
 
 // ---- launchers (defined in the .cu files) ----------------------------
 
+// Kernels launched by the library (process-wide); every launcher adds its launches.
+void count_launches(int k);
+
 cudaError_t launch_prep(const PrepParams& p, cudaStream_t s);
 cudaError_t launch_gray(const GrayParams& p, int grid, cudaStream_t s);
 int gray_blocks_per_sm(int list_cap);

@@ -375,6 +375,7 @@ cudaError_t launch_gray(const GrayParams& p, int grid, cudaStream_t s)
                                          (int)gray_smem_bytes(kMaxN, p.list_cap));
     if (e != cudaSuccess) return e;
     gray_kernel<<<grid, kGrayThreads, smem, s>>>(p);
+    count_launches(1);
     return cudaGetLastError();
 }
 

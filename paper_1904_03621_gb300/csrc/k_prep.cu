@@ -290,6 +290,7 @@ cudaError_t launch_prep(const PrepParams& p, cudaStream_t s)
     cudaError_t e = cudaFuncSetAttribute(prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     prep_kernel<<<1, kPrepThreads, smem, s>>>(p);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -301,12 +302,14 @@ cudaError_t launch_seed(const Prep* prep, int n, int free_bits, unsigned long lo
     cudaError_t e = cudaFuncSetAttribute(seed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     seed_kernel<<<blocks, kSeedThreads, smem, s>>>(prep, n, free_bits, hiconst, sample, per_block, cap, outE, outC);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_set_tau(const int* E, int S, WsHeader* hdr, cudaStream_t s)
 {
     set_tau_kernel<<<1, 1, 0, s>>>(E, S, hdr);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -322,10 +325,12 @@ cudaError_t launch_direct(const void* J, const void* h, int n, int dtype, int S,
         e = cudaFuncSetAttribute(direct_kernel<long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         direct_kernel<long long><<<1, kDirectThreads, smem, s>>>(J, h, n, dtype, S, free_bits, hiconst, energies, states);
+        count_launches(1);
     } else {
         e = cudaFuncSetAttribute(direct_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         direct_kernel<double><<<1, kDirectThreads, smem, s>>>(J, h, n, dtype, S, free_bits, hiconst, energies, states);
+        count_launches(1);
     }
     return cudaGetLastError();
 }

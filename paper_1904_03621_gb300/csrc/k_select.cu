@@ -178,6 +178,7 @@ cudaError_t launch_merge_round(const int* inE, const unsigned long long* inC, in
     cudaError_t e = cudaFuncSetAttribute(merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     merge_kernel<<<(nin + 1) / 2, kMergeThreads, smem, s>>>(inE, inC, nin, outE, outC, cap, S, W, hdr);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -189,6 +190,7 @@ cudaError_t launch_absorb_spill(int* E, unsigned long long* C, int nlists, int c
     cudaError_t e = cudaFuncSetAttribute(absorb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     absorb_kernel<<<nlists, kMergeThreads, smem, s>>>(E, C, nlists, cap, S, W, spill_E, spill_C, spill_cap, hdr);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -199,15 +201,18 @@ cudaError_t launch_finalize(const int* E, const unsigned long long* C, int cap, 
     (void)hdr;
     if (dtype == 0) {
         finalize_int_kernel<<<(S + 255) / 256, 256, 0, s>>>(E, C, S, q, static_cast<long long*>(energies), states);
+        count_launches(1);
         return cudaGetLastError();
     }
     rescore_kernel<<<(cap + 7) / 8, 256, 0, s>>>(E, C, cap, n, dtype, J, h, rescore);
+    count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     size_t smem = (size_t)cap * 16;
     e = cudaFuncSetAttribute(finalize_float_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     finalize_float_kernel<<<1, kMergeThreads, smem, s>>>(C, rescore, cap, S, static_cast<double*>(energies), states);
+    count_launches(1);
     return cudaGetLastError();
 }
 
