@@ -129,6 +129,33 @@ bf_status bf_low_spectrum(const void* J, const void* h, int n, int S, bf_dtype d
                           const bf_options* opt, void* stream);
 
 /*
+ * bf_low_spectrum_noalloc -- bf_low_spectrum for callers that cannot
+ * allocate device memory.  The paper has no counterpart; this is an
+ * interface convenience.
+ * Some callers must not allocate when they search: code running under a
+ * framework whose caching allocator owns the free device memory, callbacks
+ * and real-time loops where an allocation's implicit device synchronisation
+ * is not acceptable, or hosts whose memory budget is fixed at start-up.  This
+ * entry point takes inputs and outputs only (same meaning, layout and
+ * ownership as bf_low_spectrum) and uses a workspace held in a 4 MiB device
+ * array of the library, which every GPU that loads the library keeps until
+ * the process exits.  It calls no cudaMalloc / cudaFree.
+ *   - The first call on a device (with that device current) looks up the
+ *     array's device address once; make that first call before any stream
+ *     capture.
+ *   - Searches needing more than 4 MiB (at the default grid roughly S > 256,
+ *     or a spill area larger than opt->spill_log2, default 16 here) return
+ *     BF_EUNSUPPORTED without launching anything.
+ *   - Every call shares the array: calls whose work overlaps on the GPU race
+ *     and give undefined results.  Each call clears what it needs.
+ *   - Unlike bf_low_spectrum, the call waits for its work to finish and
+ *     returns the device-side status (BF_EOVERFLOW etc.) directly.
+ */
+bf_status bf_low_spectrum_noalloc(const void* J, const void* h, int n, int S, bf_dtype dtype,
+                                  void* energies, uint64_t* states,
+                                  const bf_options* opt, void* stream);
+
+/*
  * Synchronises `stream` and returns the status recorded on the device by the
  * last call that used `workspace` (BF_OK, BF_EOVERFLOW or BF_ETIMEOUT).
  */

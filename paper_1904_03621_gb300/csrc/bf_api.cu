@@ -135,6 +135,10 @@ cudaError_t merge_tree(int* AE, unsigned long long* AC, int* BE, unsigned long l
 
 }  // namespace
 
+namespace bf {
+bf_status report(bf_status s, const char* detail) { return fail(s, "%s", detail); }
+}  // namespace bf
+
 extern "C" {
 
 size_t bf_workspace_size(int n, int S, bf_dtype dtype, const bf_options* opt)

@@ -16,6 +16,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "bf.h"
+
 namespace bf {
 
 constexpr int kMaxN = 64;
@@ -159,6 +161,8 @@ struct PrepParams {
 
 // Kernels launched by the library (process-wide); every launcher adds its launches.
 void count_launches(int k);
+// Set the calling thread's error detail (bf_last_error_detail) and return `s`.
+bf_status report(bf_status s, const char* detail);
 
 cudaError_t launch_prep(const PrepParams& p, cudaStream_t s);
 cudaError_t launch_gray(const GrayParams& p, int grid, cudaStream_t s);
