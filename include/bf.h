@@ -155,6 +155,45 @@ bf_status bf_low_spectrum_noalloc(const void* J, const void* h, int n, int S, bf
                                   void* energies, uint64_t* states,
                                   const bf_options* opt, void* stream);
 
+/* Limits of the batched search. */
+#define BF_BATCHED_MIN_N 10
+#define BF_BATCHED_MAX_N 32
+#define BF_BATCHED_MAX_S 64
+
+/*
+ * Workspace bytes needed by bf_low_spectrum_batched for B instances of at most
+ * n_max spins; 0 for arguments it would reject.
+ */
+size_t bf_batched_workspace_size(int B, int n_max, int S, bf_dtype dtype, const bf_options* opt);
+
+/*
+ * bf_low_spectrum_batched -- the S lowest (energy, configuration) pairs of
+ * each of B independent instances (Algorithm 1, Sec. 3, applied per
+ * instance; energy of Eq. (1), Sec. 2), in one persistent launch over an
+ * (instance, chunk) work queue.
+ *   J_packed   device, instance b's n[b] x n[b] row-major couplings start at
+ *              element J_offsets[b] (strict upper triangle read)
+ *   J_offsets  device, B element offsets (int64)
+ *   h_packed   device, instance b's fields start at element h_offsets[b]
+ *   h_offsets  device, B element offsets (int64)
+ *   n          device, B spin counts, each in [BF_BATCHED_MIN_N, n_max]
+ *   n_max      host, upper bound of n[] (<= BF_BATCHED_MAX_N); sizes the workspace
+ *   S          1 <= S <= BF_BATCHED_MAX_S (and <= 2^n[b])
+ *   energies   device out, B x S row-major: int64 for BF_I32, double otherwise
+ *   states     device out, B x S configuration integers
+ *   workspace  device, >= bf_batched_workspace_size(...) bytes, 256-byte aligned
+ * opt->task_log2 sets log2 of the configurations per work unit (default 22),
+ * opt->grid_blocks the persistent grid.  No host synchronisation and no
+ * allocation: the call is capturable in a CUDA graph.  Instances with n out
+ * of range are reported by bf_workspace_status as BF_EINVAL (their output
+ * rows are left unwritten).
+ */
+bf_status bf_low_spectrum_batched(int B, const void* J_packed, const int64_t* J_offsets,
+                                  const void* h_packed, const int64_t* h_offsets, const int32_t* n,
+                                  int n_max, int S, bf_dtype dtype, void* energies, uint64_t* states,
+                                  void* workspace, size_t workspace_bytes, const bf_options* opt,
+                                  void* stream);
+
 /*
  * Synchronises `stream` and returns the status recorded on the device by the
  * last call that used `workspace` (BF_OK, BF_EOVERFLOW or BF_ETIMEOUT).

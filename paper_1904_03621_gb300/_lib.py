@@ -15,7 +15,8 @@ BF_I32, BF_F32, BF_F64 = 0, 1, 2
 BF_VARIANT_AUTO, BF_VARIANT_GRAY = 0, 1
 
 # every symbol include/bf.h declares
-EXPORTS = ["bf_workspace_size", "bf_low_spectrum", "bf_low_spectrum_noalloc", "bf_workspace_status",
+EXPORTS = ["bf_workspace_size", "bf_low_spectrum", "bf_low_spectrum_noalloc", "bf_batched_workspace_size",
+           "bf_low_spectrum_batched", "bf_workspace_status",
            "bf_last_profile", "bf_launch_count", "bf_status_string", "bf_last_error_detail", "bf_version"]
 
 
@@ -52,6 +53,11 @@ def load(path: str | None = None):
     lib.bf_low_spectrum.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, sz, ctypes.POINTER(Options), vp]
     lib.bf_low_spectrum_noalloc.restype = i32
     lib.bf_low_spectrum_noalloc.argtypes = [vp, vp, i32, i32, i32, vp, vp, ctypes.POINTER(Options), vp]
+    lib.bf_batched_workspace_size.restype = sz
+    lib.bf_batched_workspace_size.argtypes = [i32, i32, i32, i32, ctypes.POINTER(Options)]
+    lib.bf_low_spectrum_batched.restype = i32
+    lib.bf_low_spectrum_batched.argtypes = [i32, vp, vp, vp, vp, vp, i32, i32, i32, vp, vp, vp, sz,
+                                            ctypes.POINTER(Options), vp]
     lib.bf_workspace_status.restype = i32
     lib.bf_workspace_status.argtypes = [vp, vp]
     lib.bf_status_string.restype = ctypes.c_char_p

@@ -94,3 +94,65 @@ def last_profile_ms() -> float:
 def launch_count() -> int:
     """Kernels launched by libbf in this process so far."""
     return int(_lib.load().bf_launch_count())
+
+
+_NP = {torch.int32: np.int32, torch.float32: np.float32, torch.float64: np.float64}
+
+
+def pack_batch(instance_list, dtype: torch.dtype = torch.float64, device="cuda"):
+    """Pack [(J, h, ...), ...] into the device arrays bf_low_spectrum_batched takes.
+
+    Returns (J_packed, J_offsets, h_packed, h_offsets, n, n_max); integer couplings are
+    carried exactly when dtype is float64.
+    """
+    from . import instances as inst
+    n, Jp, Jo, hp, ho = inst.pack(instance_list, dtype=_NP[dtype])
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)  # noqa: E731
+    return t(Jp), t(Jo), t(hp), t(ho), t(n), int(n.max())
+
+
+def batched_workspace_size(B: int, n_max: int, S: int, dtype: torch.dtype, **opts) -> int:
+    lib = _lib.load()
+    o = _options(**opts)
+    nbytes = lib.bf_batched_workspace_size(B, n_max, S, _DTYPES[dtype], ctypes.byref(o))
+    if nbytes == 0:
+        raise _lib.BFError(_lib.BF_EINVAL, lib.bf_last_error_detail().decode())
+    return int(nbytes)
+
+
+def low_spectrum_batched(J_packed, J_offsets, h_packed, h_offsets, n, S: int, *, n_max: int,
+                         task_log2: int = 0, grid_blocks: int = 0, stream=None,
+                         workspace: torch.Tensor | None = None, check: bool = True, out: tuple | None = None):
+    """S lowest (energy, configuration) pairs of each of B instances in one launch sequence.
+
+    All tensors live on the same CUDA device: J_packed / h_packed (int32, float32 or
+    float64), J_offsets / h_offsets (int64 element offsets), n (int32 spin counts).
+    Returns (energies (B, S), states (B, S)).  With check=False nothing synchronises,
+    so the call can be captured in a CUDA graph (pass workspace and out then).
+    """
+    lib = _lib.load()
+    dt = J_packed.dtype
+    if dt not in _DTYPES or h_packed.dtype != dt:
+        raise TypeError("J_packed and h_packed must share one of int32, float32, float64")
+    B = n.shape[0]
+    o = _options(0, 0, 0, task_log2, grid_blocks)
+    nbytes = lib.bf_batched_workspace_size(B, n_max, S, _DTYPES[dt], ctypes.byref(o))
+    if nbytes == 0:
+        raise _lib.BFError(_lib.BF_EINVAL, lib.bf_last_error_detail().decode())
+    if workspace is None or workspace.numel() < nbytes:
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device=J_packed.device)
+    if out is not None:
+        energies, states = out
+    else:
+        edt = torch.int64 if dt == torch.int32 else torch.float64
+        energies = torch.empty(B, S, dtype=edt, device=J_packed.device)
+        states = torch.empty(B, S, dtype=torch.int64, device=J_packed.device)
+    sh = _stream_handle(stream)
+    st = lib.bf_low_spectrum_batched(B, J_packed.data_ptr(), J_offsets.data_ptr(), h_packed.data_ptr(),
+                                     h_offsets.data_ptr(), n.data_ptr(), n_max, S, _DTYPES[dt],
+                                     energies.data_ptr(), states.data_ptr(), workspace.data_ptr(),
+                                     workspace.numel(), ctypes.byref(o), sh)
+    _lib.check(st, lib)
+    if check:
+        _lib.check(lib.bf_workspace_status(workspace.data_ptr(), sh), lib)
+    return energies, states

@@ -272,6 +272,7 @@ bf_status bf_workspace_status(const void* workspace, void* stream_ptr)
         return fail(BF_EOVERFLOW, "candidate storage exhausted (device status 0x%x)", status);
     if (status & bf::kErrTimeout) return fail(BF_ETIMEOUT, "bounded device wait expired (device status 0x%x)", status);
     if (status & bf::kErrRange) return fail(BF_EUNSUPPORTED, "instance outside the fixed-point range (0x%x)", status);
+    if (status & bf::kErrArg) return fail(BF_EINVAL, "an instance's n is outside the supported range (0x%x)", status);
     return BF_OK;
 }
 
@@ -304,5 +305,117 @@ const char* bf_status_string(bf_status s)
 const char* bf_last_error_detail(void) { return g_detail.c_str(); }
 
 const char* bf_version(void) { return "libbf 0.1 (sm_103a)"; }
+
+}  // extern "C"
+
+// ---- batched search ----------------------------------------------------------
+
+namespace {
+
+struct BPlan {
+    int B, n_max, S, dtype, m_cap, pool_cap, final_len, grid;
+    size_t off_inst, off_tau, off_count, off_order, off_unit, off_poolE, off_poolC, total;
+};
+
+bf_status make_bplan(int B, int n_max, int S, int dtype, const bf_options* opt, BPlan& bp)
+{
+    bf_options o{};
+    if (opt) o = *opt;
+    if (B < 1) return fail(BF_EINVAL, "B=%d < 1", B);
+    if (n_max < bf::kBMinN || n_max > bf::kBMaxN)
+        return fail(BF_EUNSUPPORTED, "n_max=%d outside [%d, %d] of the batched search", n_max, bf::kBMinN, bf::kBMaxN);
+    if (dtype != BF_I32 && dtype != BF_F32 && dtype != BF_F64) return fail(BF_EINVAL, "unknown dtype %d", dtype);
+    if (S < 1) return fail(BF_EINVAL, "S=%d < 1", S);
+    if (S > bf::kBMaxS) return fail(BF_EUNSUPPORTED, "S=%d exceeds %d for the batched search", S, bf::kBMaxS);
+    if (o.task_log2 < 0 || o.grid_blocks < 0) return fail(BF_EINVAL, "negative task_log2 or grid_blocks");
+    bp = BPlan{};
+    bp.B = B;
+    bp.n_max = n_max;
+    bp.S = S;
+    bp.dtype = dtype;
+    // a work unit is 128 walks of 2^(8+m) configurations: 2^(15+m) per unit
+    bp.m_cap = o.task_log2 ? std::min(std::max(o.task_log2 - 15, 0), 16) : 7;
+    const int ubits = std::max(0, n_max - 15 - bp.m_cap);
+    const long long units_max = 1ll << ubits;
+    long long pool = units_max * S + 512;
+    if (pool > 8192) pool = 8192;
+    bp.pool_cap = (int)pool;
+    bp.final_len = bf::next_pow2(bp.pool_cap);
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "device query");
+    const int bps = bf::batched_walker_blocks_per_sm();
+    if (bps < 1) return fail(BF_ECUDA, "batched walker does not fit on an SM");
+    bp.grid = o.grid_blocks ? o.grid_blocks : sms * bps;
+    size_t off = bf::align_up(sizeof(bf::WsHeader), 256);
+    bp.off_inst = off;  off = bf::align_up(off + (size_t)B * sizeof(bf::BInst), 256);
+    bp.off_tau = off;   off = bf::align_up(off + (size_t)B * 4, 256);
+    bp.off_count = off; off = bf::align_up(off + (size_t)B * 4, 256);
+    bp.off_order = off; off = bf::align_up(off + (size_t)B * 4, 256);
+    bp.off_unit = off;  off = bf::align_up(off + (size_t)(B + 1) * 8, 256);
+    bp.off_poolE = off; off = bf::align_up(off + (size_t)B * bp.pool_cap * 4, 256);
+    bp.off_poolC = off; off = bf::align_up(off + (size_t)B * bp.pool_cap * 8, 256);
+    bp.total = off;
+    return BF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t bf_batched_workspace_size(int B, int n_max, int S, bf_dtype dtype, const bf_options* opt)
+{
+    BPlan bp;
+    if (make_bplan(B, n_max, S, dtype, opt, bp) != BF_OK) return 0;
+    return bp.total;
+}
+
+bf_status bf_low_spectrum_batched(int B, const void* J_packed, const int64_t* J_offsets, const void* h_packed,
+                                  const int64_t* h_offsets, const int32_t* n, int n_max, int S, bf_dtype dtype,
+                                  void* energies, uint64_t* states, void* workspace, size_t workspace_bytes,
+                                  const bf_options* opt, void* stream_ptr)
+{
+    g_detail.clear();
+    BPlan bp;
+    bf_status st = make_bplan(B, n_max, S, dtype, opt, bp);
+    if (st != BF_OK) return st;
+    if (!J_packed || !J_offsets || !h_packed || !h_offsets || !n || !energies || !states || !workspace)
+        return fail(BF_EINVAL, "null pointer argument");
+    if (workspace_bytes < bp.total)
+        return fail(BF_EWORKSPACE, "workspace of %zu bytes < %zu required", workspace_bytes, bp.total);
+    if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return fail(BF_EWORKSPACE, "workspace not 256-byte aligned");
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    char* ws = static_cast<char*>(workspace);
+    auto* hdr = reinterpret_cast<bf::WsHeader*>(ws);
+    cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(bf::WsHeader), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "header reset");
+    bf::BatchParams p{};
+    p.B = B;
+    p.n_max = n_max;
+    p.S = S;
+    p.dtype = dtype;
+    p.m_cap = bp.m_cap;
+    p.pool_cap = bp.pool_cap;
+    p.final_len = bp.final_len;
+    p.J = J_packed;
+    p.h = h_packed;
+    p.J_off = reinterpret_cast<const long long*>(J_offsets);
+    p.h_off = reinterpret_cast<const long long*>(h_offsets);
+    p.n = n;
+    p.hdr = hdr;
+    p.inst = reinterpret_cast<bf::BInst*>(ws + bp.off_inst);
+    p.tau = reinterpret_cast<int*>(ws + bp.off_tau);
+    p.pool_count = reinterpret_cast<unsigned*>(ws + bp.off_count);
+    p.order = reinterpret_cast<int*>(ws + bp.off_order);
+    p.unit_off = reinterpret_cast<unsigned long long*>(ws + bp.off_unit);
+    p.pool_E = reinterpret_cast<int*>(ws + bp.off_poolE);
+    p.pool_C = reinterpret_cast<unsigned long long*>(ws + bp.off_poolC);
+    p.energies = energies;
+    p.states = reinterpret_cast<unsigned long long*>(states);
+    e = bf::launch_batched(p, bp.grid, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batched kernels");
+    return BF_OK;
+}
 
 }  // extern "C"

@@ -37,7 +37,8 @@ enum : unsigned {
     kErrSpill = 1u,      // spill area exhausted: records were lost
     kErrWindow = 2u,     // more near-ties than a list can hold
     kErrTimeout = 4u,    // bounded wait gave up
-    kErrRange = 8u       // instance outside the supported fixed-point range
+    kErrRange = 8u,      // instance outside the supported fixed-point range
+    kErrArg = 16u        // invalid per-instance argument found on the device (batched call)
 };
 
 // Workspace header, first 256 bytes of the workspace.
@@ -47,7 +48,7 @@ struct alignas(16) WsHeader {
     unsigned long long task_next;     // dynamic task counter of the enumeration kernel
     unsigned spill_count;             // records written to the spill area
     unsigned pad0;
-    unsigned long long magic;         // set by every call, checked by bf_workspace_status
+    unsigned long long total_units;   // batched call: work units in the queue
     unsigned pad[56];
 };
 static_assert(sizeof(WsHeader) == 256, "header size");
@@ -156,6 +157,45 @@ struct PrepParams {
     Prep* prep;
     WsHeader* hdr;
 };
+
+// ---- batched search ----------------------------------------------------
+
+constexpr int kBMinN = 10;                       // smallest n of the batched walker
+constexpr int kBMaxN = 32;                       // largest n of the batched walker
+constexpr int kBMaxS = 64;
+
+struct BInst {                                   // per-instance constants (device)
+    int n, q, W, m, nh, status;
+    unsigned long long units;                    // work units (128 tasks each)
+    double delta, emax;
+    int Jq[kBMaxN * kBMaxN];
+    int hq[kBMaxN];
+    int T[kInnerSteps];
+    unsigned dT16[kInnerSteps];
+    int col[kBMaxN][16];
+};
+
+struct BatchParams {
+    int B, n_max, S, dtype, m_cap, pool_cap, final_len, pad0;
+    const void* J;
+    const void* h;
+    const long long* J_off;
+    const long long* h_off;
+    const int* n;
+    WsHeader* hdr;
+    BInst* inst;
+    int* tau;
+    unsigned* pool_count;
+    int* order;
+    unsigned long long* unit_off;
+    int* pool_E;
+    unsigned long long* pool_C;
+    void* energies;
+    unsigned long long* states;
+};
+
+cudaError_t launch_batched(const BatchParams& p, int walker_grid, cudaStream_t s);
+int batched_walker_blocks_per_sm();
 
 // ---- launchers (defined in the .cu files) ----------------------------
 

@@ -1,0 +1,658 @@
+// Batched search (step A6): thousands of independent instances of uneven n
+// in one persistent launch over an (instance, chunk) work queue.
+//
+// Every instance gets the single-instance treatment of k_prep.cu / k_gray.cu
+// (exact fixed point, Gray walk with the two-lane 16-bit pre-filter, exact
+// rescans), with these changes so that the whole sequence needs no host
+// synchronisation and can be captured in a CUDA graph:
+//   - the per-instance inner increments live in a shared-memory slot of the
+//     warp processing the instance (loaded with 128-bit loads, LSU pipe)
+//     instead of kernel parameters;
+//   - a work unit is one warp: 32 lanes x 4 walks = 128 tasks of
+//     2^(8+m) configurations; warps pop units from a queue ordered by
+//     decreasing n (largest instances first);
+//   - hits are collected warp-cooperatively: a flagged walk is rescanned by
+//     all 32 lanes (8 configurations each) into a bounded per-warp buffer that
+//     is merged (warp bitonic sort, keep rule) before it can overflow, so no
+//     spill area is needed;
+//   - each unit appends its surviving records to the instance's pool and
+//     lowers the instance threshold with atomicMin; a final kernel reselects
+//     each instance's S lowest (FP64 re-evaluation for float instances).
+#include <cfloat>
+#include <climits>
+#include <utility>
+
+#include "bf_internal.cuh"
+#include "bf_sort.cuh"
+#include "bf_walk.cuh"
+
+namespace bf {
+namespace {
+
+constexpr int kBWarps = 4;                    // warps per block of the walker
+constexpr int kBThreads = kBWarps * 32;
+constexpr int kBBuf = 512;                    // records per warp buffer
+constexpr int kBSeed = 1024;                  // sampled configurations per instance for its first threshold
+constexpr int kBSeedThreads = 256;
+
+__device__ __forceinline__ double load_value(const void* p, int dtype, size_t idx)
+{
+    if (dtype == 0) return (double)static_cast<const int*>(p)[idx];
+    if (dtype == 1) return (double)static_cast<const float*>(p)[idx];
+    return static_cast<const double*>(p)[idx];
+}
+
+__device__ double block_sum(double v, double* red)
+{
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = blockDim.x >> 1; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+// ---- per-instance preparation: one block per instance -----------------------
+
+__global__ void __launch_bounds__(kBSeedThreads) bprep_kernel(const BatchParams p)
+{
+    __shared__ double Jd[kBMaxN * kBMaxN];
+    __shared__ double hd[kBMaxN];
+    __shared__ double red[kBSeedThreads];
+    __shared__ int Jq[kBMaxN * kBMaxN];
+    __shared__ int hq[kBMaxN];
+    __shared__ int Tq[kInnerSteps];
+    __shared__ int sE[kBSeed];
+    __shared__ unsigned long long sC[kBSeed];
+    __shared__ int s_q, s_status;
+    __shared__ double s_emax;
+
+    const int b = blockIdx.x, tid = threadIdx.x;
+    BInst* I = p.inst + b;
+    const int n = p.n[b];
+    if (n < kBMinN || n > p.n_max || n > kBMaxN || (1ll << n) < p.S) {
+        if (tid == 0) {
+            I->n = n;
+            I->status = kErrArg;
+            I->units = 0;
+            atomicOr(&p.hdr->status, kErrArg);
+            p.tau[b] = INT_MIN;
+            p.pool_count[b] = 0u;
+        }
+        return;
+    }
+    const long long jo = p.J_off[b], ho = p.h_off[b];
+    for (int idx = tid; idx < n * n; idx += blockDim.x) {
+        int i = idx / n, j = idx % n;
+        Jd[idx] = (i < j) ? load_value(p.J, p.dtype, jo + idx) : 0.0;
+    }
+    for (int i = tid; i < n; i += blockDim.x) hd[i] = load_value(p.h, p.dtype, ho + i);
+    __syncthreads();
+    double part = 0.0;
+    for (int idx = tid; idx < n * n; idx += blockDim.x) part += fabs(Jd[idx]);
+    for (int i = tid; i < n; i += blockDim.x) part += fabs(hd[i]);
+    const double emax = block_sum(part, red);
+    if (tid == 0) {
+        int status = 0, q = 0;
+        if (emax > 0.0) {
+            int e;
+            frexp(emax, &e);
+            q = kEmqLog2 - e;
+            if (p.dtype == 0) {
+                if (q < 0) status |= kErrRange;
+                q = q > 16 ? 16 : (q < 0 ? 0 : q);
+            } else {
+                q = q > 200 ? 200 : (q < -200 ? -200 : q);
+            }
+        }
+        if (!(emax < 1e300)) status |= kErrRange;
+        s_q = q;
+        s_status = status;
+        s_emax = emax;
+    }
+    __syncthreads();
+    const int q = s_q;
+    part = 0.0;
+    for (int idx = tid; idx < n * n; idx += blockDim.x) {
+        int i = idx / n, j = idx % n;
+        int a = i < j ? i : j, c = i < j ? j : i;
+        int v = 0;
+        if (a != c) {
+            double x = Jd[a * n + c];
+            double r = rint(ldexp(x, q));
+            v = (int)r;
+            if (i < j) part += fabs(x - ldexp(r, -q));
+        }
+        Jq[idx] = v;
+    }
+    for (int i = tid; i < n; i += blockDim.x) {
+        double r = rint(ldexp(hd[i], q));
+        hq[i] = (int)r;
+        part += fabs(hd[i] - ldexp(r, -q));
+    }
+    const double delta = block_sum(part, red);
+    for (int g = tid; g < kInnerSteps; g += blockDim.x) {
+        int t = 0;
+        for (int i = 0; i < kInnerBits; i++) {
+            int si = ((g >> i) & 1) ? 1 : -1;
+            for (int k = i + 1; k < kInnerBits; k++) t += Jq[i * n + k] * si * (((g >> k) & 1) ? 1 : -1);
+        }
+        Tq[g] = t;
+    }
+    __syncthreads();
+    // first threshold: exact energies of a pseudo-random sample (all configurations if fewer)
+    const unsigned long long space = 1ull << n;
+    const int R = space < (unsigned long long)kBSeed ? (int)space : kBSeed;
+    for (int x = tid; x < kBSeed; x += blockDim.x) {
+        if (x >= R) { sE[x] = kEmptyE; sC[x] = kEmptyC; continue; }
+        unsigned long long c = (R == (int)space) ? (unsigned long long)x
+                                                 : (((unsigned long long)x * 0x9E3779B97F4A7C15ull) & (space - 1ull));
+        int e = 0;
+        for (int i = 0; i < n; i++) {
+            int row = hq[i];
+            for (int j = i + 1; j < n; j++) row += ((c >> j) & 1ull) ? Jq[i * n + j] : -Jq[i * n + j];
+            e += ((c >> i) & 1ull) ? row : -row;
+        }
+        sE[x] = e;
+        sC[x] = c;
+    }
+    block_sort(sE, sC, kBSeed);
+    // outputs
+    for (int idx = tid; idx < n * n; idx += blockDim.x) I->Jq[idx] = Jq[idx];
+    for (int i = tid; i < kBMaxN; i += blockDim.x) I->hq[i] = i < n ? hq[i] : 0;
+    for (int g = tid; g < kInnerSteps; g += blockDim.x) {
+        I->T[g] = Tq[g];
+        unsigned v = 0;
+        if (g > 0) {
+            int g1 = g ^ (g >> 1), g0 = (g - 1) ^ ((g - 1) >> 1);
+            v = (unsigned)((Tq[g1] >> 16) - (Tq[g0] >> 16)) * 65537u;
+        }
+        I->dT16[g] = v;
+    }
+    for (int idx = tid; idx < kBMaxN * 16; idx += blockDim.x) {
+        int j = idx / 16, k = idx % 16;
+        int row = k < kInnerBits + kKeep ? k : -1;
+        I->col[j][k] = (j < n && row >= 0 && row < n) ? Jq[row * n + j] : 0;
+    }
+    if (tid == 0) {
+        int status = s_status;
+        int W = 0;
+        if (p.dtype != 0 && delta > 0.0) {
+            double eps = 8.0 * (double)n * (double)n * ldexp(1.0, -53) * s_emax;
+            double w = ceil(ldexp(2.0 * delta + 2.0 * eps, q)) + 2.0;
+            if (w > (double)(1 << 28)) { w = (double)(1 << 28); status |= kErrRange; }
+            W = (int)w;
+        }
+        int m = n - kInnerBits - 7;             // 128 tasks per unit
+        m = m < 0 ? 0 : (m > p.m_cap ? p.m_cap : m);
+        const int nh = n - kInnerBits - m;
+        I->n = n;
+        I->q = q;
+        I->W = W;
+        I->m = m;
+        I->nh = nh;
+        I->status = status;
+        I->units = nh > 7 ? (1ull << (nh - 7)) : 1ull;
+        I->delta = delta;
+        I->emax = s_emax;
+        p.tau[b] = sE[p.S - 1];
+        p.pool_count[b] = 0u;
+        if (status) atomicOr(&p.hdr->status, (unsigned)status);
+    }
+}
+
+// ---- work queue: instances ordered by decreasing n, unit prefix sums --------
+
+constexpr int kPlanThreads = 1024;
+
+__global__ void __launch_bounds__(kPlanThreads) bplan_kernel(const BatchParams p)
+{
+    __shared__ unsigned cnt[kBMaxN + 1], start[kBMaxN + 1];
+    __shared__ unsigned long long part[kPlanThreads];
+    const int tid = threadIdx.x;
+    for (int i = tid; i <= kBMaxN; i += blockDim.x) cnt[i] = 0u;
+    __syncthreads();
+    // counting sort by n, largest first; invalid instances (no units) go to bucket 0
+    for (int b = tid; b < p.B; b += blockDim.x) {
+        int n = p.inst[b].n;
+        int key = (p.inst[b].status & kErrArg) ? 0 : n;
+        atomicAdd(&cnt[key], 1u);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        unsigned s = 0;
+        for (int n = kBMaxN; n >= 0; n--) { start[n] = s; s += cnt[n]; }
+    }
+    __syncthreads();
+    for (int b = tid; b < p.B; b += blockDim.x) {
+        int key = (p.inst[b].status & kErrArg) ? 0 : p.inst[b].n;
+        unsigned pos = atomicAdd(&start[key], 1u);
+        p.order[pos] = b;
+    }
+    __syncthreads();
+    // exclusive prefix sums of the unit counts in queue order
+    const int chunk = (p.B + kPlanThreads - 1) / kPlanThreads;
+    const int lo = tid * chunk, hi = min(p.B, lo + chunk);
+    unsigned long long sum = 0;
+    for (int k = lo; k < hi; k++) sum += p.inst[p.order[k]].units;
+    part[tid] = sum;
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long run = 0;
+        for (int t = 0; t < kPlanThreads; t++) { unsigned long long v = part[t]; part[t] = run; run += v; }
+        p.unit_off[p.B] = run;
+        p.hdr->task_next = 0ull;
+        p.hdr->total_units = run;
+    }
+    __syncthreads();
+    unsigned long long run = part[tid];
+    for (int k = lo; k < hi; k++) {
+        p.unit_off[k] = run;
+        run += p.inst[p.order[k]].units;
+    }
+}
+
+// ---- warp-level helpers ------------------------------------------------------
+
+__device__ void warp_sort(int* E, unsigned long long* C, int len, int lane)
+{
+    for (int size = 2; size <= len; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            __syncwarp();
+            for (int i = lane; i < (len >> 1); i += 32) {
+                int lo = 2 * stride * (i / stride) + (i % stride);
+                cmp_swap(E, C, lo, lo + stride, (lo & size) == 0);
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// Sort the buffer and keep the first S records (plus every record within W of the
+// S-th for float instances).  Returns the new count; sets the S-th key when known.
+__device__ int warp_merge(int* E, unsigned long long* C, int count, int S, int W, int& kE,
+                          unsigned long long& kC, unsigned* status, int lane)
+{
+    for (int i = count + lane; i < kBBuf; i += 32) { E[i] = kEmptyE; C[i] = kEmptyC; }
+    warp_sort(E, C, kBBuf, lane);
+    if (count < S) return count;
+    kE = E[S - 1];
+    kC = C[S - 1];
+    int keep = S;
+    if (W > 0) {
+        long long lim = (long long)kE + W;
+        keep = upper_bound_key(E, kBBuf, lim > INT_MAX - 1 ? INT_MAX - 1 : (int)lim);
+        if (keep > count) keep = count;
+        if (keep > kBBuf - kInnerSteps) {
+            keep = kBBuf - kInnerSteps;
+            if (lane == 0) atomicOr(status, kErrWindow);
+        }
+    }
+    return keep;
+}
+
+template <int t>
+__device__ __forceinline__ void bstep(Packed& w, unsigned d)
+{
+    if constexpr (t > 0) {
+        constexpr int k = cx_ctz(t);
+        constexpr bool up = cx_up(t);
+        w.Xa += (up ? w.Ga[k] : 0u - w.Ga[k]) + d;
+        w.Xb += (up ? w.Gb[k] : 0u - w.Gb[k]) + d;
+        w.M = __vminu2(__vminu2(w.M, w.Xa), w.Xb);
+    }
+}
+
+// four steps per 128-bit shared-memory load of the instance's increments
+template <int g>
+__device__ __forceinline__ void bwalk_group(Packed& w, const uint4* tab4)
+{
+    const uint4 d = tab4[g];
+    bstep<4 * g + 0>(w, d.x);
+    bstep<4 * g + 1>(w, d.y);
+    bstep<4 * g + 2>(w, d.z);
+    bstep<4 * g + 3>(w, d.w);
+}
+
+template <int... Gs>
+__device__ __forceinline__ void bwalk_block(Packed& w, const uint4* tab4, std::integer_sequence<int, Gs...>)
+{
+    (bwalk_group<Gs>(w, tab4), ...);
+}
+
+}  // namespace
+
+// ---- the persistent walker ------------------------------------------------------
+
+__global__ void __launch_bounds__(kBThreads, 3) bwalk_kernel(const BatchParams p)
+{
+    __shared__ __align__(16) unsigned s_dT[kBWarps][kInnerSteps];
+    __shared__ int s_T[kBWarps][kInnerSteps];
+    __shared__ int s_E[kBWarps][kBBuf];
+    __shared__ unsigned long long s_C[kBWarps][kBBuf];
+
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned* dTw = s_dT[wid];
+    int* Tw = s_T[wid];
+    int* Ew = s_E[wid];
+    unsigned long long* Cw = s_C[wid];
+    const unsigned long long total = *(volatile unsigned long long*)&p.hdr->total_units;
+    const int S = p.S;
+
+    for (;;) {
+        unsigned long long u = 0;
+        if (lane == 0) u = atomicAdd(&p.hdr->task_next, 1ull);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if (u >= total) break;
+        // position k in the queue: unit_off[k] <= u < unit_off[k + 1]
+        int lo = 0, hi = p.B;
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (p.unit_off[mid] <= u) lo = mid; else hi = mid;
+        }
+        const int b = p.order[lo];
+        const unsigned long long lu = u - p.unit_off[lo];
+        const BInst* I = p.inst + b;
+        const int n = I->n, m = I->m, W = I->W;
+        const unsigned long long ntasks = 1ull << I->nh;
+        for (int i = lane; i < kInnerSteps; i += 32) {
+            dTw[i] = I->dT16[i];
+            Tw[i] = I->T[i];
+        }
+        __syncwarp();
+
+        // walks of this lane: tasks lu * 128 + lane * 4 + w
+        int E0[kWalks], G[kWalks][kInnerBits], Fm[kWalks][kKeep];
+        unsigned long long cfg0[kWalks];
+        unsigned active_mask = 0;
+        const int walk_shift = kInnerBits + m;
+#pragma unroll
+        for (int w = 0; w < kWalks; w++) {
+            unsigned long long task = lu * 128ull + (unsigned long long)(lane * kWalks + w);
+            if (task < ntasks) active_mask |= 1u << w; else task = 0;
+            const unsigned long long c = task << walk_shift;
+            cfg0[w] = c;
+            int e = 0;
+            for (int i = 0; i < n; i++) {
+                int row = I->hq[i];
+                for (int j = i + 1; j < n; j++) row += ((c >> j) & 1ull) ? I->Jq[i * n + j] : -I->Jq[i * n + j];
+                e += ((c >> i) & 1ull) ? row : -row;
+            }
+            E0[w] = e;
+#pragma unroll
+            for (int k = 0; k < kInnerBits; k++) {
+                int f = I->hq[k];
+                for (int j = kInnerBits; j < n; j++) f += ((c >> j) & 1ull) ? I->Jq[k * n + j] : -I->Jq[k * n + j];
+                G[w][k] = 2 * f;
+            }
+#pragma unroll
+            for (int r = 0; r < kKeep; r++) {
+                const int l = kInnerBits + r;
+                int f = l < n ? I->hq[l] : 0;
+                if (l < n)
+                    for (int j = 0; j < n; j++) f += ((c >> j) & 1ull) ? I->Jq[l * n + j] : -I->Jq[l * n + j];
+                Fm[w][r] = f;
+            }
+        }
+        Packed pk;
+#pragma unroll
+        for (int k = 0; k < kInnerBits; k++) {
+            pk.Ga[k] = pack_hi16(G[0][k], G[1][k]);
+            pk.Gb[k] = pack_hi16(G[2][k], G[3][k]);
+        }
+
+        // per-warp record list (buffer) and threshold
+        int count = 0, kE = kEmptyE;
+        unsigned long long kC = kEmptyC;
+        int tau_scr = 0;
+        unsigned thr16 = 0;
+        auto refresh = [&]() {
+            int t = min(*(volatile int*)&p.tau[b], kE);
+            long long ts = (long long)t + W;
+            tau_scr = (int)(ts > (1ll << 30) ? (1ll << 30) : ts);
+            thr16 = threshold16(tau_scr);
+        };
+        refresh();
+        unsigned long long cmid = 0ull;
+        const unsigned nblocks = 1u << m;
+        for (unsigned ub = 0; ub < nblocks; ++ub) {
+            pk.Xa = pack_energy(E0[0], E0[1]);
+            pk.Xb = pack_energy(E0[2], E0[3]);
+            pk.M = __vminu2(pk.Xa, pk.Xb);
+            bwalk_block(pk, reinterpret_cast<const uint4*>(dTw), std::make_integer_sequence<int, kInnerSteps / 4>{});
+            const unsigned flags = (((pk.M & 0xffffu) <= thr16) ? 1u : 0u) | (((pk.M >> 16) <= thr16) ? 2u : 0u);
+            const unsigned bal = __ballot_sync(0xffffffffu, flags != 0u);
+            if (bal) {
+                // warp-cooperative exact rescan of every flagged walk
+                for (unsigned rest = bal; rest; rest &= rest - 1u) {
+                    const int L = __ffs(rest) - 1;
+                    const unsigned fL = __shfl_sync(0xffffffffu, flags, L);
+                    const unsigned aL = __shfl_sync(0xffffffffu, active_mask, L);
+#pragma unroll
+                    for (int w = 0; w < kWalks; w++) {
+                        if (!((fL >> (w & 1)) & 1u) || !((aL >> w) & 1u)) continue;
+                        const int e0 = __shfl_sync(0xffffffffu, E0[w], L);
+                        int g8[kInnerBits];
+#pragma unroll
+                        for (int k = 0; k < kInnerBits; k++) g8[k] = __shfl_sync(0xffffffffu, G[w][k], L);
+                        const unsigned long long cb = __shfl_sync(0xffffffffu, cfg0[w], L) | cmid;
+                        if (count > kBBuf - kInnerSteps) {
+                            count = warp_merge(Ew, Cw, count, S, W, kE, kC, &p.hdr->status, lane);
+                            if (count >= S && lane == 0) atomicMin(&p.tau[b], kE);
+                            __syncwarp();
+                            refresh();
+                        }
+                        const unsigned base_e = (unsigned)e0 - (unsigned)Tw[0];
+#pragma unroll
+                        for (int j = 0; j < kInnerSteps / 32; j++) {
+                            const int t = j * 32 + lane;
+                            const int g = t ^ (t >> 1);
+                            unsigned acc = base_e + (unsigned)Tw[g];
+#pragma unroll
+                            for (int k = 0; k < kInnerBits; k++) acc += ((g >> k) & 1) ? (unsigned)g8[k] : 0u;
+                            const int e = (int)acc;
+                            const unsigned long long c = cb | (unsigned long long)g;
+                            const bool hit = e <= tau_scr && !(W == 0 && e == kE && c > kC);
+                            const unsigned hb = __ballot_sync(0xffffffffu, hit);
+                            if (hit) {
+                                const int slot = count + __popc(hb & ((1u << lane) - 1u));
+                                Ew[slot] = e;
+                                Cw[slot] = c;
+                            }
+                            count += __popc(hb);
+                        }
+                        __syncwarp();
+                    }
+                }
+            }
+            if ((ub & 15u) == 15u) refresh();
+            // flip one middle spin
+            if (ub + 1 < nblocks) {
+                const unsigned u1 = ub + 1;
+                const int jrel = __ffs(u1) - 1;
+                const int j = kInnerBits + jrel;
+                const bool up = ((u1 ^ (u1 >> 1)) >> jrel) & 1u;
+                int F[kWalks];
+                if (jrel < kKeep) {
+#pragma unroll
+                    for (int w = 0; w < kWalks; w++) {
+                        int f = Fm[w][0];
+#pragma unroll
+                        for (int r = 1; r < kKeep; r++) f = (jrel == r) ? Fm[w][r] : f;
+                        F[w] = f;
+                    }
+                } else {
+#pragma unroll
+                    for (int w = 0; w < kWalks; w++) {
+                        const unsigned long long c = cfg0[w] | cmid;
+                        int f = I->hq[j];
+                        for (int i = 0; i < n; i++) f += ((c >> i) & 1ull) ? I->Jq[j * n + i] : -I->Jq[j * n + i];
+                        F[w] = f;
+                    }
+                }
+                int colv[kInnerBits + kKeep];
+#pragma unroll
+                for (int k = 0; k < kInnerBits + kKeep; k++) colv[k] = I->col[j][k];
+#pragma unroll
+                for (int w = 0; w < kWalks; w++) {
+                    const unsigned dE = (unsigned)F[w] << 1;
+                    E0[w] = (int)((unsigned)E0[w] + (up ? dE : 0u - dE));
+#pragma unroll
+                    for (int k = 0; k < kInnerBits; k++) {
+                        const unsigned d = (unsigned)colv[k] << 2;
+                        G[w][k] = (int)((unsigned)G[w][k] + (up ? d : 0u - d));
+                    }
+#pragma unroll
+                    for (int r = 0; r < kKeep; r++) {
+                        const unsigned d = (unsigned)colv[kInnerBits + r] << 1;
+                        Fm[w][r] = (int)((unsigned)Fm[w][r] + (up ? d : 0u - d));
+                    }
+                }
+                cmid ^= 1ull << j;
+#pragma unroll
+                for (int k = 0; k < kInnerBits; k++) {
+                    pk.Ga[k] = pack_hi16(G[0][k], G[1][k]);
+                    pk.Gb[k] = pack_hi16(G[2][k], G[3][k]);
+                }
+            }
+        }
+        // end of unit: final merge, publish the threshold, append surviving records to the pool
+        if (count > 0) {
+            count = warp_merge(Ew, Cw, count, S, W, kE, kC, &p.hdr->status, lane);
+            if (count >= S && lane == 0) atomicMin(&p.tau[b], kE);
+            __syncwarp();
+            const int tcur = min(*(volatile int*)&p.tau[b], kE);
+            const long long lim = (long long)tcur + W;
+            // the list is sorted: records up to the limit form a prefix
+            int keep = 0;
+            for (int i = lane; i < count; i += 32) keep += ((long long)Ew[i] <= lim) ? 1 : 0;
+            for (int o = 16; o > 0; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
+            unsigned base = 0;
+            if (lane == 0 && keep > 0) base = atomicAdd(&p.pool_count[b], (unsigned)keep);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            for (int i = lane; i < keep; i += 32) {
+                const unsigned slot = base + (unsigned)i;
+                if (slot < (unsigned)p.pool_cap) {
+                    p.pool_E[(size_t)b * p.pool_cap + slot] = Ew[i];
+                    p.pool_C[(size_t)b * p.pool_cap + slot] = Cw[i];
+                } else {
+                    atomicOr(&p.hdr->status, kErrSpill);
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+namespace {
+
+// ---- per-instance final selection: one block per instance -----------------------
+
+constexpr int kBFinalThreads = 512;
+
+__global__ void __launch_bounds__(kBFinalThreads) bfinal_kernel(const BatchParams p)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int b = blockIdx.x;
+    const BInst* I = p.inst + b;
+    const int len = p.final_len;                      // power of two >= pool_cap
+    unsigned long long* C = reinterpret_cast<unsigned long long*>(smem);
+    int* E = reinterpret_cast<int*>(C + len);
+    double* E64 = reinterpret_cast<double*>(E + len);  // aligned: len is a power of two >= 2
+    __shared__ int s_keep;
+    const int S = p.S;
+    if (I->status & kErrArg) return;
+    unsigned cnt = *(volatile unsigned*)&p.pool_count[b];
+    if (cnt > (unsigned)p.pool_cap) cnt = p.pool_cap;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+        bool ok = i < (int)cnt;
+        E[i] = ok ? p.pool_E[(size_t)b * p.pool_cap + i] : kEmptyE;
+        C[i] = ok ? p.pool_C[(size_t)b * p.pool_cap + i] : kEmptyC;
+    }
+    block_sort(E, C, len);
+    if (threadIdx.x == 0) {
+        int valid = upper_bound_key(E, len, INT_MAX - 1);
+        int keep = valid < S ? valid : S;
+        if (valid >= S && I->W > 0) {
+            long long lim = (long long)E[S - 1] + I->W;
+            keep = upper_bound_key(E, len, lim > INT_MAX - 1 ? INT_MAX - 1 : (int)lim);
+        }
+        if (valid < S) atomicOr(&p.hdr->status, kErrSpill);   // cannot happen unless records were lost
+        s_keep = keep;
+    }
+    __syncthreads();
+    const int keep = s_keep;
+    const int n = I->n;
+    if (p.dtype == 0) {
+        for (int k = threadIdx.x; k < S; k += blockDim.x) {
+            static_cast<long long*>(p.energies)[(size_t)b * S + k] = k < keep ? (long long)(E[k] >> I->q) : LLONG_MAX;
+            p.states[(size_t)b * S + k] = C[k];
+        }
+        return;
+    }
+    // FP64 re-evaluation of Eq. (1) for the kept records, then reselection by (E, c)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const long long jo = p.J_off[b], ho = p.h_off[b];
+    for (int r = warp; r < len; r += nw) {
+        if (r >= keep) {
+            if (lane == 0) E64[r] = DBL_MAX;
+            continue;
+        }
+        const unsigned long long c = C[r];
+        double part = 0.0;
+        for (int i = lane; i < n; i += 32) {
+            double row = load_value(p.h, p.dtype, ho + i);
+            for (int j = i + 1; j < n; j++) {
+                double v = load_value(p.J, p.dtype, jo + (long long)i * n + j);
+                row += ((c >> j) & 1ull) ? v : -v;
+            }
+            part += ((c >> i) & 1ull) ? row : -row;
+        }
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (lane == 0) E64[r] = part;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < len; i += blockDim.x)
+        if (i >= keep) C[i] = kEmptyC;
+    block_sort(E64, C, len);
+    for (int k = threadIdx.x; k < S; k += blockDim.x) {
+        static_cast<double*>(p.energies)[(size_t)b * S + k] = E64[k];
+        p.states[(size_t)b * S + k] = C[k];
+    }
+}
+
+}  // namespace
+
+int batched_walker_blocks_per_sm()
+{
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, bwalk_kernel, kBThreads, 0) != cudaSuccess) return 0;
+    return blocks;
+}
+
+cudaError_t launch_batched(const BatchParams& p, int walker_grid, cudaStream_t s)
+{
+    bprep_kernel<<<p.B, kBSeedThreads, 0, s>>>(p);
+    count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    bplan_kernel<<<1, kPlanThreads, 0, s>>>(p);
+    count_launches(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    bwalk_kernel<<<walker_grid, kBThreads, 0, s>>>(p);
+    count_launches(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    size_t smem = (size_t)p.final_len * 20;
+    e = cudaFuncSetAttribute(bfinal_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    bfinal_kernel<<<p.B, kBFinalThreads, smem, s>>>(p);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace bf
