@@ -195,6 +195,26 @@ bf_status bf_low_spectrum_batched(int B, const void* J_packed, const int64_t* J_
                                   void* stream);
 
 /*
+ * bf_low_spectrum_backward -- gradient of L = sum_b sum_k g[b,k] E_b(s^(b,k))
+ * with respect to each instance's couplings and fields.  Eq. (1) (Sec. 2) is
+ * linear in J and h, so dL/dJ_ij = sum_k g_k s_i s_j (i < j) and
+ * dL/dh_i = sum_k g_k s_i over the given states (FP64 accumulation, k in
+ * ascending order).
+ *   states     device, B x S configuration integers (e.g. a forward's output)
+ *   grad_E     device, B x S doubles (dL/dE of each returned energy)
+ *   n          device, B spin counts (1..64)
+ *   J_offsets  device, B int64 element offsets of each instance's n x n block in dJ
+ *   h_offsets  device, B int64 element offsets of each instance's n fields in dh
+ *   dJ, dh     device out, float or double per out_dtype (BF_F32 / BF_F64);
+ *              entries on and below the diagonal of each dJ block are set to 0
+ *   S          1 <= S <= 4096
+ * No host synchronisation, no allocation; capturable.
+ */
+bf_status bf_low_spectrum_backward(const uint64_t* states, const double* grad_E, const int32_t* n, int B, int S,
+                                   const int64_t* J_offsets, const int64_t* h_offsets, void* dJ, void* dh,
+                                   bf_dtype out_dtype, void* stream);
+
+/*
  * Synchronises `stream` and returns the status recorded on the device by the
  * last call that used `workspace` (BF_OK, BF_EOVERFLOW or BF_ETIMEOUT).
  */

@@ -156,3 +156,80 @@ def low_spectrum_batched(J_packed, J_offsets, h_packed, h_offsets, n, S: int, *,
     if check:
         _lib.check(lib.bf_workspace_status(workspace.data_ptr(), sh), lib)
     return energies, states
+
+
+def low_spectrum_backward(states, grad_E, n, J_offsets, h_offsets, dJ_numel: int, dh_numel: int,
+                          dtype: torch.dtype = torch.float64, stream=None):
+    """dL/dJ (strict upper triangles, packed like J) and dL/dh for L = sum g[b,k] E_b(states[b,k]).
+
+    states (B, S) int64 holding uint64 configurations, grad_E (B, S) float64, n (B,) int32,
+    offsets int64; returns (dJ, dh) flat tensors of the given dtype.
+    """
+    lib = _lib.load()
+    B, S = states.shape
+    dev = states.device
+    dJ = torch.empty(dJ_numel, dtype=dtype, device=dev)
+    dh = torch.empty(dh_numel, dtype=dtype, device=dev)
+    g = grad_E.to(torch.float64).contiguous()
+    st = lib.bf_low_spectrum_backward(states.contiguous().data_ptr(), g.data_ptr(), n.data_ptr(), B, S,
+                                      J_offsets.data_ptr(), h_offsets.data_ptr(), dJ.data_ptr(), dh.data_ptr(),
+                                      _lib.BF_F64 if dtype == torch.float64 else _lib.BF_F32,
+                                      _stream_handle(stream))
+    _lib.check(st, lib)
+    return dJ, dh
+
+
+class LowSpectrumFn(torch.autograd.Function):
+    """energies, states = LowSpectrumFn.apply(J, h, S).
+
+    Forward: the S lowest energies (float64) and configurations of one float instance.
+    Backward: dL/dJ (strict upper triangle; the diagonal and lower triangle get 0, as
+    they do not enter the energy) and dL/dh, computed by the backward kernel from the
+    saved states.
+    """
+
+    @staticmethod
+    def forward(ctx, J, h, S):
+        en, st = low_spectrum(J, h, S)
+        ctx.save_for_backward(st)
+        ctx.n = J.shape[0]
+        ctx.jdtype, ctx.hdtype = J.dtype, h.dtype
+        ctx.mark_non_differentiable(st)
+        return en, st
+
+    @staticmethod
+    def backward(ctx, g_en, g_st):
+        (st,) = ctx.saved_tensors
+        n = ctx.n
+        dev = st.device
+        if g_en is None:
+            g_en = torch.zeros(st.shape[0], dtype=torch.float64, device=dev)
+        nt = torch.tensor([n], dtype=torch.int32, device=dev)
+        zero = torch.zeros(1, dtype=torch.int64, device=dev)
+        dJ, dh = low_spectrum_backward(st.view(1, -1), g_en.view(1, -1), nt, zero, zero, n * n, n)
+        return dJ.view(n, n).to(ctx.jdtype), dh.to(ctx.hdtype), None
+
+
+class LowSpectrumBatchedFn(torch.autograd.Function):
+    """energies (B, S), states = LowSpectrumBatchedFn.apply(J_packed, h_packed, J_offsets, h_offsets, n, S, n_max).
+
+    Batched forward (bf_low_spectrum_batched) and the hand-written backward kernel;
+    gradients are returned packed like J_packed and h_packed.
+    """
+
+    @staticmethod
+    def forward(ctx, J_packed, h_packed, J_offsets, h_offsets, n, S, n_max):
+        en, st = low_spectrum_batched(J_packed, J_offsets, h_packed, h_offsets, n, S, n_max=n_max)
+        ctx.save_for_backward(st, n, J_offsets, h_offsets)
+        ctx.sizes = (J_packed.numel(), h_packed.numel(), J_packed.dtype, h_packed.dtype)
+        ctx.mark_non_differentiable(st)
+        return en.to(torch.float64), st
+
+    @staticmethod
+    def backward(ctx, g_en, g_st):
+        st, n, J_offsets, h_offsets = ctx.saved_tensors
+        nj, nh, jdt, hdt = ctx.sizes
+        if g_en is None:
+            g_en = torch.zeros(st.shape, dtype=torch.float64, device=st.device)
+        dJ, dh = low_spectrum_backward(st, g_en, n, J_offsets, h_offsets, nj, nh)
+        return dJ.to(jdt), dh.to(hdt), None, None, None, None, None

@@ -419,3 +419,19 @@ bf_status bf_low_spectrum_batched(int B, const void* J_packed, const int64_t* J_
 }
 
 }  // extern "C"
+
+extern "C" bf_status bf_low_spectrum_backward(const uint64_t* states, const double* grad_E, const int32_t* n, int B,
+                                              int S, const int64_t* J_offsets, const int64_t* h_offsets, void* dJ,
+                                              void* dh, bf_dtype out_dtype, void* stream_ptr)
+{
+    g_detail.clear();
+    if (B < 1 || S < 1) return fail(BF_EINVAL, "B=%d, S=%d must be >= 1", B, S);
+    if (S > 4096) return fail(BF_EUNSUPPORTED, "S=%d exceeds 4096 for the backward kernel", S);
+    if (out_dtype != BF_F32 && out_dtype != BF_F64) return fail(BF_EINVAL, "out_dtype must be BF_F32 or BF_F64");
+    if (!states || !grad_E || !n || !J_offsets || !h_offsets || !dJ || !dh) return fail(BF_EINVAL, "null pointer argument");
+    cudaError_t e = bf::launch_backward(reinterpret_cast<const unsigned long long*>(states), grad_E, n, B, S,
+                                        reinterpret_cast<const long long*>(J_offsets),
+                                        reinterpret_cast<const long long*>(h_offsets), dJ, dh,
+                                        out_dtype == BF_F64 ? 1 : 0, static_cast<cudaStream_t>(stream_ptr));
+    return e == cudaSuccess ? BF_OK : cuda_fail(e, "backward kernel");
+}

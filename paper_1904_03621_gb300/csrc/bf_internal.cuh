@@ -195,6 +195,9 @@ struct BatchParams {
 };
 
 cudaError_t launch_batched(const BatchParams& p, int walker_grid, cudaStream_t s);
+cudaError_t launch_backward(const unsigned long long* states, const double* g, const int* n, int B, int S,
+                            const long long* J_off, const long long* h_off, void* dJ, void* dh, int out_f64,
+                            cudaStream_t s);
 int batched_walker_blocks_per_sm();
 
 // ---- launchers (defined in the .cu files) ----------------------------
