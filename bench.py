@@ -164,6 +164,81 @@ def run_reference(args, rank, world):
     return 0
 
 
+def batched_section(api, torch, dev, steps, warmup):
+    """4096-instance batch (graph-replayed) vs plain single-instance calls, and the backward
+    kernel vs a plain PyTorch gradient on the same states."""
+    from paper_1904_03621_gb300 import instances
+    insts = instances.batched_4096()
+    J, Jo, h, ho, n, n_max = api.pack_batch(insts, device=dev)
+    S = 10
+    B = len(insts)
+    configs = float(sum(2.0 ** t[0].shape[0] for t in insts))
+    ws = torch.empty(api.batched_workspace_size(B, n_max, S, torch.float64), dtype=torch.uint8, device=dev)
+    en = torch.empty(B, S, dtype=torch.float64, device=dev)
+    st = torch.empty(B, S, dtype=torch.int64, device=dev)
+    api.low_spectrum_batched(J, Jo, h, ho, n, S, n_max=n_max, workspace=ws, out=(en, st))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        api.low_spectrum_batched(J, Jo, h, ho, n, S, n_max=n_max, workspace=ws, out=(en, st), check=False)
+    for _ in range(warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    from paper_1904_03621_gb300 import _lib
+    lib = _lib.load()
+    _lib.check(lib.bf_workspace_status(ws.data_ptr(), None), lib)
+    # plain path: one bf_low_spectrum call per instance (first 64 instances of each kind)
+    sample = list(range(64)) + list(range(B // 2, B // 2 + 64))
+    t0 = time.perf_counter()
+    for i in sample:
+        Ji, hi_, _ = insts[i]
+        api.low_spectrum(torch.from_numpy(np.asarray(Ji, dtype=np.float64)).to(dev),
+                         torch.from_numpy(np.asarray(hi_, dtype=np.float64)).to(dev), S)
+    torch.cuda.synchronize()
+    plain_ips = len(sample) / (time.perf_counter() - t0)
+    out = {"workload": "batched_4096: 2048 dense (n~U{16..28}, J~N(0,1), h~N(0,0.5^2)) + 2048 Chimera "
+                       "(n~U{16..28}, J=+-1, h=0), S=10, one graph-replayed launch sequence",
+           "instances_per_s": B / (ms * 1e-3), "configs_per_s": configs / (ms * 1e-3), "ms_per_step": ms,
+           "steps": steps, "plain_instances_per_s": plain_ips,
+           "plain_sample": f"{len(sample)} instances, one bf_low_spectrum call each",
+           "speedup_vs_plain": (B / (ms * 1e-3)) / plain_ips}
+    # backward: 256 x n=28 (FP32), S=32
+    ginst, w = instances.grad_256()
+    Jg, Jgo, hg, hgo, ng, ngm = api.pack_batch(ginst, dtype=torch.float32, device=dev)
+    eng, stg = api.low_spectrum_batched(Jg, Jgo, hg, hgo, ng, 32, n_max=ngm)
+    wt = torch.from_numpy(w).to(dev)
+    for _ in range(2):
+        api.low_spectrum_backward(stg, wt, ng, Jgo, hgo, Jg.numel(), hg.numel(), dtype=torch.float32)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        api.low_spectrum_backward(stg, wt, ng, Jgo, hgo, Jg.numel(), hg.numel(), dtype=torch.float32)
+    e1.record()
+    torch.cuda.synchronize()
+    back_ms = e0.elapsed_time(e1) / steps
+    bits = ((stg.unsqueeze(-1) >> torch.arange(28, device=dev)) & 1).to(torch.float64) * 2 - 1  # (B, S, n)
+    for _ in range(2):
+        torch.einsum("bk,bki,bkj->bij", wt, bits, bits).triu(1)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        spins = ((stg.unsqueeze(-1) >> torch.arange(28, device=dev)) & 1).to(torch.float64) * 2 - 1
+        torch.einsum("bk,bki,bkj->bij", wt, spins, spins).triu(1)
+        torch.einsum("bk,bki->bi", wt, spins)
+    e1.record()
+    torch.cuda.synchronize()
+    plain_back_ms = e0.elapsed_time(e1) / steps
+    out["backward"] = {"workload": "grad_256: 256 x n=28, S=32, L=sum w_k E_k", "backward_ms": back_ms,
+                       "plain_torch_backward_ms": plain_back_ms, "speedup_vs_plain": plain_back_ms / back_ms}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -172,6 +247,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="float_n48")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -284,6 +360,8 @@ def main():
         "gpu_launches": int(launches),
         "timed_region_s": region_s,
     }
+    if not args.no_batched:
+        line["batched"] = batched_section(api, torch, dev, max(args.steps, 3), max(args.warmup, 3))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(J, h, S)
     if rank == 0:

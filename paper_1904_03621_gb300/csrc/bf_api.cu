@@ -313,7 +313,7 @@ const char* bf_version(void) { return "libbf 0.1 (sm_103a)"; }
 namespace {
 
 struct BPlan {
-    int B, n_max, S, dtype, m_cap, pool_cap, final_len, grid;
+    int B, n_max, S, dtype, m_cap, pool_cap, final_len, grid, max_waves;
     size_t off_inst, off_tau, off_count, off_order, off_unit, off_poolE, off_poolC, total;
 };
 
@@ -333,9 +333,9 @@ bf_status make_bplan(int B, int n_max, int S, int dtype, const bf_options* opt, 
     bp.n_max = n_max;
     bp.S = S;
     bp.dtype = dtype;
-    // a work unit is 128 walks of 2^(8+m) configurations: 2^(15+m) per unit
-    bp.m_cap = o.task_log2 ? std::min(std::max(o.task_log2 - 15, 0), 16) : 7;
-    const int ubits = std::max(0, n_max - 15 - bp.m_cap);
+    // a work unit is 2^10 walks of 2^(9+m) configurations: 2^(19+m) per unit
+    bp.m_cap = o.task_log2 ? std::min(std::max(o.task_log2 - 19, 0), 16) : 6;
+    const int ubits = std::max(0, n_max - 19 - bp.m_cap);
     const long long units_max = 1ll << ubits;
     long long pool = units_max * S + 512;
     if (pool > 8192) pool = 8192;
@@ -353,7 +353,8 @@ bf_status make_bplan(int B, int n_max, int S, int dtype, const bf_options* opt, 
     bp.off_tau = off;   off = bf::align_up(off + (size_t)B * 4, 256);
     bp.off_count = off; off = bf::align_up(off + (size_t)B * 4, 256);
     bp.off_order = off; off = bf::align_up(off + (size_t)B * 4, 256);
-    bp.off_unit = off;  off = bf::align_up(off + (size_t)(B + 1) * 8, 256);
+    bp.max_waves = (int)units_max;
+    bp.off_unit = off;  off = bf::align_up(off + (size_t)(units_max + 1) * 8, 256);
     bp.off_poolE = off; off = bf::align_up(off + (size_t)B * bp.pool_cap * 4, 256);
     bp.off_poolC = off; off = bf::align_up(off + (size_t)B * bp.pool_cap * 8, 256);
     bp.total = off;
@@ -408,7 +409,8 @@ bf_status bf_low_spectrum_batched(int B, const void* J_packed, const int64_t* J_
     p.tau = reinterpret_cast<int*>(ws + bp.off_tau);
     p.pool_count = reinterpret_cast<unsigned*>(ws + bp.off_count);
     p.order = reinterpret_cast<int*>(ws + bp.off_order);
-    p.unit_off = reinterpret_cast<unsigned long long*>(ws + bp.off_unit);
+    p.wave_off = reinterpret_cast<unsigned long long*>(ws + bp.off_unit);
+    p.max_waves = bp.max_waves;
     p.pool_E = reinterpret_cast<int*>(ws + bp.off_poolE);
     p.pool_C = reinterpret_cast<unsigned long long*>(ws + bp.off_poolC);
     p.energies = energies;

@@ -21,7 +21,7 @@
 namespace bf {
 
 constexpr int kMaxN = 64;
-constexpr int kInnerBits = 8;                    // spins walked inside one unrolled block
+constexpr int kInnerBits = 9;                    // spins walked inside one unrolled block
 constexpr int kInnerSteps = 1 << kInnerBits;     // configurations per block and walk
 constexpr int kKeep = 4;                         // middle spins whose local field is kept in registers
 constexpr int kWalks = 4;                        // walks (tasks) per thread: two packed words
@@ -70,7 +70,7 @@ struct Prep {
     int Jq[kMaxN * kMaxN];        // quantised symmetric couplings, zero diagonal
     int hq[kMaxN];
     int T[kInnerSteps];           // exact inner pair energy T[g] (quantised units)
-    int colJ[kMaxN][16];          // column j: J_q[k][j] for k < 8, then J_q[8 + r][j] for r < 4
+    int colJ[kMaxN][16];          // column j: J_q[k][j] for the inner spins k, then the kept middle spins
 };
 
 // Records: quantised energy (int32) + configuration (uint64), kept in two
@@ -131,7 +131,7 @@ __host__ inline Layout make_layout(int S, int max_blocks, int spill_log2)
 // ---- kernel parameter blocks -------------------------------------------
 
 struct GrayParams {
-    unsigned dT16[kInnerSteps];     // index t = 1..255; entry 0 unused
+    unsigned dT16[kInnerSteps];     // index t = 1..kInnerSteps-1; entry 0 unused
     int n, m, nh;                   // spins, walked middle spins, task-index bits
     int free_bits;
     unsigned long long hiconst;     // fixed top bits of every configuration
@@ -187,7 +187,8 @@ struct BatchParams {
     int* tau;
     unsigned* pool_count;
     int* order;
-    unsigned long long* unit_off;
+    unsigned long long* wave_off;                // max_waves + 1 entries
+    int max_waves, pad1;
     int* pool_E;
     unsigned long long* pool_C;
     void* energies;

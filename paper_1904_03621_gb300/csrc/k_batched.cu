@@ -8,9 +8,11 @@
 //   - the per-instance inner increments live in a shared-memory slot of the
 //     warp processing the instance (loaded with 128-bit loads, LSU pipe)
 //     instead of kernel parameters;
-//   - a work unit is one warp: 32 lanes x 4 walks = 128 tasks of
-//     2^(8+m) configurations; warps pop units from a queue ordered by
-//     decreasing n (largest instances first);
+//   - a work unit is one block: 256 threads x 4 walks = 1024 tasks of
+//     2^(9+m) configurations; blocks pop units from a queue of waves (unit w
+//     of every instance, instances by decreasing n), and a barrier after every
+//     unrolled block keeps the block's warps on the same stretch of code
+//     (independent warps stalled on instruction fetch);
 //   - hits are collected warp-cooperatively: a flagged walk is rescanned by
 //     all 32 lanes (8 configurations each) into a bounded per-warp buffer that
 //     is merged (warp bitonic sort, keep rule) before it can overflow, so no
@@ -29,11 +31,14 @@
 namespace bf {
 namespace {
 
-constexpr int kBWarps = 4;                    // warps per block of the walker
+constexpr int kBWarps = 8;                    // warps per block of the walker
 constexpr int kBThreads = kBWarps * 32;
-constexpr int kBBuf = 512;                    // records per warp buffer
+constexpr int kBUnitWalkBits = 10;            // a work unit: 2^10 walks (256 threads x 4)
+constexpr int kBBuf = 2 * kInnerSteps;       // records per warp buffer (room for one walk's rescan)
 constexpr int kBSeed = 1024;                  // sampled configurations per instance for its first threshold
 constexpr int kBSeedThreads = 256;
+constexpr size_t kBWarpSmem = (size_t)kBBuf * 12;                 // record buffer bytes per warp
+constexpr size_t kBSmem = kBWarpSmem * kBWarps + (size_t)kInnerSteps * 8;   // + the unit's tables
 
 __device__ __forceinline__ double load_value(const void* p, int dtype, size_t idx)
 {
@@ -143,21 +148,61 @@ __global__ void __launch_bounds__(kBSeedThreads) bprep_kernel(const BatchParams 
         Tq[g] = t;
     }
     __syncthreads();
-    // first threshold: exact energies of a pseudo-random sample (all configurations if fewer)
+    // first threshold.  n >= 18: each of the 256 threads Gray-walks its own 2^10 configurations
+    // (low 10 spins free, the rest fixed to a distinct pattern) and keeps the lowest; the
+    // S-th lowest of those 256 minima bounds the S-th energy of the instance from above.
+    // Smaller n: exact energies of a pseudo-random sample of 1024 (all if fewer).
     const unsigned long long space = 1ull << n;
-    const int R = space < (unsigned long long)kBSeed ? (int)space : kBSeed;
-    for (int x = tid; x < kBSeed; x += blockDim.x) {
-        if (x >= R) { sE[x] = kEmptyE; sC[x] = kEmptyC; continue; }
-        unsigned long long c = (R == (int)space) ? (unsigned long long)x
-                                                 : (((unsigned long long)x * 0x9E3779B97F4A7C15ull) & (space - 1ull));
+    if (n >= 18) {
+        const unsigned long long hi_mask = (space >> 10) - 1ull;
+        for (int x = tid; x < kBSeed; x += blockDim.x) { sE[x] = kEmptyE; sC[x] = kEmptyC; }
+        __syncthreads();
+        const unsigned long long hi = ((unsigned long long)tid * 0x9E3779B97F4A7C15ull) & hi_mask;
+        unsigned long long c = hi << 10;
         int e = 0;
         for (int i = 0; i < n; i++) {
             int row = hq[i];
             for (int j = i + 1; j < n; j++) row += ((c >> j) & 1ull) ? Jq[i * n + j] : -Jq[i * n + j];
             e += ((c >> i) & 1ull) ? row : -row;
         }
-        sE[x] = e;
-        sC[x] = c;
+        int f[10];
+        for (int k = 0; k < 10; k++) {          // local fields of the walked spins (all -1 now)
+            int v = hq[k];
+            for (int j = 0; j < n; j++) v += ((c >> j) & 1ull) ? Jq[k * n + j] : -Jq[k * n + j];
+            f[k] = v;
+        }
+        int best = e;
+        unsigned long long bestc = c;
+        for (int t = 1; t < 1024; t++) {
+            const int k = __ffs(t) - 1;
+            const bool up = (((t ^ (t >> 1)) >> k) & 1) != 0;
+            int fk = 0;
+            for (int r = 0; r < 10; r++) fk = (r == k) ? f[r] : fk;
+            e += up ? 2 * fk : -2 * fk;
+            c ^= 1ull << k;
+            for (int r = 0; r < 10; r++) {
+                const int d = 2 * Jq[r * n + k];
+                f[r] += (r == k) ? 0 : (up ? d : -d);
+            }
+            if (e < best) { best = e; bestc = c; }
+        }
+        sE[tid] = best;
+        sC[tid] = bestc;
+    } else {
+        const int R = space < (unsigned long long)kBSeed ? (int)space : kBSeed;
+        for (int x = tid; x < kBSeed; x += blockDim.x) {
+            if (x >= R) { sE[x] = kEmptyE; sC[x] = kEmptyC; continue; }
+            unsigned long long c = (R == (int)space) ? (unsigned long long)x
+                                                     : (((unsigned long long)x * 0x9E3779B97F4A7C15ull) & (space - 1ull));
+            int e = 0;
+            for (int i = 0; i < n; i++) {
+                int row = hq[i];
+                for (int j = i + 1; j < n; j++) row += ((c >> j) & 1ull) ? Jq[i * n + j] : -Jq[i * n + j];
+                e += ((c >> i) & 1ull) ? row : -row;
+            }
+            sE[x] = e;
+            sC[x] = c;
+        }
     }
     block_sort(sE, sC, kBSeed);
     // outputs
@@ -186,7 +231,7 @@ __global__ void __launch_bounds__(kBSeedThreads) bprep_kernel(const BatchParams 
             if (w > (double)(1 << 28)) { w = (double)(1 << 28); status |= kErrRange; }
             W = (int)w;
         }
-        int m = n - kInnerBits - 7;             // 128 tasks per unit
+        int m = n - kInnerBits - kBUnitWalkBits;   // 2^10 tasks per unit
         m = m < 0 ? 0 : (m > p.m_cap ? p.m_cap : m);
         const int nh = n - kInnerBits - m;
         I->n = n;
@@ -195,7 +240,7 @@ __global__ void __launch_bounds__(kBSeedThreads) bprep_kernel(const BatchParams 
         I->m = m;
         I->nh = nh;
         I->status = status;
-        I->units = nh > 7 ? (1ull << (nh - 7)) : 1ull;
+        I->units = nh > kBUnitWalkBits ? (1ull << (nh - kBUnitWalkBits)) : 1ull;
         I->delta = delta;
         I->emax = s_emax;
         p.tau[b] = sE[p.S - 1];
@@ -211,7 +256,6 @@ constexpr int kPlanThreads = 1024;
 __global__ void __launch_bounds__(kPlanThreads) bplan_kernel(const BatchParams p)
 {
     __shared__ unsigned cnt[kBMaxN + 1], start[kBMaxN + 1];
-    __shared__ unsigned long long part[kPlanThreads];
     const int tid = threadIdx.x;
     for (int i = tid; i <= kBMaxN; i += blockDim.x) cnt[i] = 0u;
     __syncthreads();
@@ -233,25 +277,35 @@ __global__ void __launch_bounds__(kPlanThreads) bplan_kernel(const BatchParams p
         p.order[pos] = b;
     }
     __syncthreads();
-    // exclusive prefix sums of the unit counts in queue order
-    const int chunk = (p.B + kPlanThreads - 1) / kPlanThreads;
-    const int lo = tid * chunk, hi = min(p.B, lo + chunk);
-    unsigned long long sum = 0;
-    for (int k = lo; k < hi; k++) sum += p.inst[p.order[k]].units;
-    part[tid] = sum;
+    // waves: unit w of every instance that has more than w units, instances in queue order
+    // (units are non-increasing along the order, so each wave is a prefix of it); a later
+    // unit of an instance then starts from the threshold its earlier units produced
+    __shared__ unsigned hist[64];
+    for (int i = tid; i < 64; i += blockDim.x) hist[i] = 0u;
     __syncthreads();
-    if (tid == 0) {
-        unsigned long long run = 0;
-        for (int t = 0; t < kPlanThreads; t++) { unsigned long long v = part[t]; part[t] = run; run += v; }
-        p.unit_off[p.B] = run;
-        p.hdr->task_next = 0ull;
-        p.hdr->total_units = run;
+    for (int k = tid; k < p.B; k += blockDim.x) {
+        const unsigned long long un = p.inst[p.order[k]].units;
+        if (un == 0) continue;
+        atomicAdd(&hist[63 - __clzll(un)], 1u);          // units are powers of two
     }
     __syncthreads();
-    unsigned long long run = part[tid];
-    for (int k = lo; k < hi; k++) {
-        p.unit_off[k] = run;
-        run += p.inst[p.order[k]].units;
+    if (tid == 0) {
+        unsigned long long max_units = 0;
+        for (int L = 0; L < 64; L++) if (hist[L]) max_units = 1ull << L;
+        unsigned long long w_cap = (unsigned long long)p.max_waves;
+        if (max_units > w_cap) { max_units = w_cap; atomicOr(&p.hdr->status, kErrArg); }
+        unsigned long long run = 0, count = 0;
+        for (int L = 0; L < 64; L++) count += hist[L];     // instances with >= 1 unit
+        int L = 0;
+        for (unsigned long long w = 0; w < max_units; w++) {
+            while (L < 64 && (1ull << L) <= w) { count -= hist[L]; L++; }
+            p.wave_off[w] = run;
+            run += count;
+        }
+        p.wave_off[max_units] = run;
+        p.hdr->task_next = 0ull;
+        p.hdr->total_units = run;
+        p.hdr->pad[0] = (unsigned)max_units;
     }
 }
 
@@ -276,15 +330,17 @@ __device__ void warp_sort(int* E, unsigned long long* C, int len, int lane)
 __device__ int warp_merge(int* E, unsigned long long* C, int count, int S, int W, int& kE,
                           unsigned long long& kC, unsigned* status, int lane)
 {
-    for (int i = count + lane; i < kBBuf; i += 32) { E[i] = kEmptyE; C[i] = kEmptyC; }
-    warp_sort(E, C, kBBuf, lane);
+    int len = 64;
+    while (len < count) len <<= 1;                   // count <= kBBuf
+    for (int i = count + lane; i < len; i += 32) { E[i] = kEmptyE; C[i] = kEmptyC; }
+    warp_sort(E, C, len, lane);
     if (count < S) return count;
     kE = E[S - 1];
     kC = C[S - 1];
     int keep = S;
     if (W > 0) {
         long long lim = (long long)kE + W;
-        keep = upper_bound_key(E, kBBuf, lim > INT_MAX - 1 ? INT_MAX - 1 : (int)lim);
+        keep = upper_bound_key(E, len, lim > INT_MAX - 1 ? INT_MAX - 1 : (int)lim);
         if (keep > count) keep = count;
         if (keep > kBBuf - kInnerSteps) {
             keep = kBBuf - kInnerSteps;
@@ -327,51 +383,51 @@ __device__ __forceinline__ void bwalk_block(Packed& w, const uint4* tab4, std::i
 
 // ---- the persistent walker ------------------------------------------------------
 
-__global__ void __launch_bounds__(kBThreads, 3) bwalk_kernel(const BatchParams p)
+__global__ void __launch_bounds__(kBThreads, 2) bwalk_kernel(const BatchParams p)
 {
-    __shared__ __align__(16) unsigned s_dT[kBWarps][kInnerSteps];
-    __shared__ int s_T[kBWarps][kInnerSteps];
-    __shared__ int s_E[kBWarps][kBBuf];
-    __shared__ unsigned long long s_C[kBWarps][kBBuf];
-
+    // dynamic shared memory: per warp C[kBBuf], E[kBBuf]; then the unit's dT16[kInnerSteps], T[kInnerSteps]
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned* dTw = s_dT[wid];
-    int* Tw = s_T[wid];
-    int* Ew = s_E[wid];
-    unsigned long long* Cw = s_C[wid];
+    unsigned long long* Cw = reinterpret_cast<unsigned long long*>(smem_raw + (size_t)wid * kBWarpSmem);
+    int* Ew = reinterpret_cast<int*>(Cw + kBBuf);
+    unsigned* dTw = reinterpret_cast<unsigned*>(smem_raw + kBWarpSmem * kBWarps);
+    int* Tw = reinterpret_cast<int*>(dTw + kInnerSteps);
+    __shared__ unsigned long long s_unit;
+    __shared__ int s_count[kBWarps];
     const unsigned long long total = *(volatile unsigned long long*)&p.hdr->total_units;
     const int S = p.S;
 
     for (;;) {
-        unsigned long long u = 0;
-        if (lane == 0) u = atomicAdd(&p.hdr->task_next, 1ull);
-        u = __shfl_sync(0xffffffffu, u, 0);
+        if (threadIdx.x == 0) s_unit = atomicAdd(&p.hdr->task_next, 1ull);
+        __syncthreads();
+        const unsigned long long u = s_unit;
         if (u >= total) break;
-        // position k in the queue: unit_off[k] <= u < unit_off[k + 1]
-        int lo = 0, hi = p.B;
+        // wave w: wave_off[w] <= u < wave_off[w + 1]; the unit is unit w of the instance at
+        // position u - wave_off[w] of the queue order
+        int lo = 0, hi = (int)p.hdr->pad[0];
         while (hi - lo > 1) {
             int mid = (lo + hi) >> 1;
-            if (p.unit_off[mid] <= u) lo = mid; else hi = mid;
+            if (p.wave_off[mid] <= u) lo = mid; else hi = mid;
         }
-        const int b = p.order[lo];
-        const unsigned long long lu = u - p.unit_off[lo];
+        const int b = p.order[u - p.wave_off[lo]];
+        const unsigned long long lu = (unsigned long long)lo;
         const BInst* I = p.inst + b;
         const int n = I->n, m = I->m, W = I->W;
         const unsigned long long ntasks = 1ull << I->nh;
-        for (int i = lane; i < kInnerSteps; i += 32) {
+        for (int i = threadIdx.x; i < kInnerSteps; i += blockDim.x) {
             dTw[i] = I->dT16[i];
             Tw[i] = I->T[i];
         }
-        __syncwarp();
+        __syncthreads();
 
-        // walks of this lane: tasks lu * 128 + lane * 4 + w
+        // walks of this thread: tasks lu * 2^10 + threadIdx.x * 4 + w
         int E0[kWalks], G[kWalks][kInnerBits], Fm[kWalks][kKeep];
         unsigned long long cfg0[kWalks];
         unsigned active_mask = 0;
         const int walk_shift = kInnerBits + m;
 #pragma unroll
         for (int w = 0; w < kWalks; w++) {
-            unsigned long long task = lu * 128ull + (unsigned long long)(lane * kWalks + w);
+            unsigned long long task = (lu << kBUnitWalkBits) + (unsigned long long)(threadIdx.x * kWalks + w);
             if (task < ntasks) active_mask |= 1u << w; else task = 0;
             const unsigned long long c = task << walk_shift;
             cfg0[w] = c;
@@ -467,8 +523,16 @@ __global__ void __launch_bounds__(kBThreads, 3) bwalk_kernel(const BatchParams p
                         __syncwarp();
                     }
                 }
+                // tighten at once: the warp's S-th record bounds the instance's S-th energy
+                if (count >= S) {
+                    count = warp_merge(Ew, Cw, count, S, W, kE, kC, &p.hdr->status, lane);
+                    if (lane == 0) atomicMin(&p.tau[b], kE);
+                    __syncwarp();
+                    refresh();
+                }
             }
-            if ((ub & 15u) == 15u) refresh();
+            if ((ub & 3u) == 3u) refresh();
+            __syncthreads();   // keep the block's warps on the same stretch of the unrolled code
             // flip one middle spin
             if (ub + 1 < nblocks) {
                 const unsigned u1 = ub + 1;
@@ -519,31 +583,56 @@ __global__ void __launch_bounds__(kBThreads, 3) bwalk_kernel(const BatchParams p
                 }
             }
         }
-        // end of unit: final merge, publish the threshold, append surviving records to the pool
+        // end of unit: every warp sorts its records, warp 0 merges the 8 lists and appends
+        // the block's survivors to the instance pool (at most S plus the float window)
         if (count > 0) {
             count = warp_merge(Ew, Cw, count, S, W, kE, kC, &p.hdr->status, lane);
             if (count >= S && lane == 0) atomicMin(&p.tau[b], kE);
-            __syncwarp();
-            const int tcur = min(*(volatile int*)&p.tau[b], kE);
-            const long long lim = (long long)tcur + W;
-            // the list is sorted: records up to the limit form a prefix
-            int keep = 0;
-            for (int i = lane; i < count; i += 32) keep += ((long long)Ew[i] <= lim) ? 1 : 0;
-            for (int o = 16; o > 0; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
-            unsigned base = 0;
-            if (lane == 0 && keep > 0) base = atomicAdd(&p.pool_count[b], (unsigned)keep);
-            base = __shfl_sync(0xffffffffu, base, 0);
-            for (int i = lane; i < keep; i += 32) {
-                const unsigned slot = base + (unsigned)i;
-                if (slot < (unsigned)p.pool_cap) {
-                    p.pool_E[(size_t)b * p.pool_cap + slot] = Ew[i];
-                    p.pool_C[(size_t)b * p.pool_cap + slot] = Cw[i];
-                } else {
-                    atomicOr(&p.hdr->status, kErrSpill);
+        }
+        if (lane == 0) s_count[wid] = count;
+        __syncthreads();
+        if (wid == 0) {
+            for (int w2 = 1; w2 < kBWarps; w2++) {
+                const int cw = s_count[w2];
+                if (cw == 0) continue;
+                if (count > kBBuf - kInnerSteps) {
+                    count = warp_merge(Ew, Cw, count, S, W, kE, kC, &p.hdr->status, lane);
+                    __syncwarp();
+                }
+                const unsigned long long* C2 =
+                    reinterpret_cast<const unsigned long long*>(smem_raw + (size_t)w2 * kBWarpSmem);
+                const int* E2 = reinterpret_cast<const int*>(C2 + kBBuf);
+                for (int i = lane; i < cw; i += 32) {   // cw <= kBBuf - kInnerSteps: fits
+                    Ew[count + i] = E2[i];
+                    Cw[count + i] = C2[i];
+                }
+                count += cw;
+                __syncwarp();
+            }
+            if (count > 0) {
+                count = warp_merge(Ew, Cw, count, S, W, kE, kC, &p.hdr->status, lane);
+                if (count >= S && lane == 0) atomicMin(&p.tau[b], kE);
+                __syncwarp();
+                const int tcur = min(*(volatile int*)&p.tau[b], kE);
+                const long long lim = (long long)tcur + W;
+                int keep = 0;   // the list is sorted: records up to the limit form a prefix
+                for (int i = lane; i < count; i += 32) keep += ((long long)Ew[i] <= lim) ? 1 : 0;
+                for (int o = 16; o > 0; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
+                unsigned base = 0;
+                if (lane == 0 && keep > 0) base = atomicAdd(&p.pool_count[b], (unsigned)keep);
+                base = __shfl_sync(0xffffffffu, base, 0);
+                for (int i = lane; i < keep; i += 32) {
+                    const unsigned slot = base + (unsigned)i;
+                    if (slot < (unsigned)p.pool_cap) {
+                        p.pool_E[(size_t)b * p.pool_cap + slot] = Ew[i];
+                        p.pool_C[(size_t)b * p.pool_cap + slot] = Cw[i];
+                    } else {
+                        atomicOr(&p.hdr->status, kErrSpill);
+                    }
                 }
             }
         }
-        __syncwarp();
+        __syncthreads();   // every warp is done with this unit's tables
     }
 }
 
@@ -629,7 +718,10 @@ __global__ void __launch_bounds__(kBFinalThreads) bfinal_kernel(const BatchParam
 int batched_walker_blocks_per_sm()
 {
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, bwalk_kernel, kBThreads, 0) != cudaSuccess) return 0;
+    const size_t smem = kBSmem;
+    if (cudaFuncSetAttribute(bwalk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, bwalk_kernel, kBThreads, smem) != cudaSuccess) return 0;
     return blocks;
 }
 
@@ -643,7 +735,9 @@ cudaError_t launch_batched(const BatchParams& p, int walker_grid, cudaStream_t s
     count_launches(1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    bwalk_kernel<<<walker_grid, kBThreads, 0, s>>>(p);
+    e = cudaFuncSetAttribute(bwalk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBSmem);
+    if (e != cudaSuccess) return e;
+    bwalk_kernel<<<walker_grid, kBThreads, kBSmem, s>>>(p);
     count_launches(1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

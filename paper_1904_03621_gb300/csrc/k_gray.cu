@@ -9,13 +9,13 @@
 // dE = 2 s_new F_k (F_k the local field on the flipped spin k).
 //
 // Bit layout of a configuration c (bit i = spin i, 1 = +1):
-//   [0, 8)         inner spins: walked by a fully unrolled 255-step block
-//   [8, 8+m)       middle spins: walked one flip per block (dynamic index)
-//   [8+m, free)    task index (prefix) of the walk
+//   [0, 9)         inner spins: walked by a fully unrolled 511-step block
+//   [9, 9+m)       middle spins: walked one flip per block (dynamic index)
+//   [9+m, free)    task index (prefix) of the walk
 //   [free, n)      fixed bits (subspace mode, Sec. 3, Eq. (6))
 //
 // Arithmetic: the quantised instance is exact in int32.  Per walk we keep
-// E0 (energy with all inner spins at -1), G_k = 2 F_k for the 8 inner spins
+// E0 (energy with all inner spins at -1), G_k = 2 F_k for the 9 inner spins
 // (fields from non-inner spins) and the local fields of 4 middle spins.
 // Inside a block, E(g) = E0 + sum_{k in g} G_k + T[g] - T[0].  The unrolled
 // walk runs on 16-bit values floor((E + 2^31) / 2^16), two walks packed per
@@ -23,7 +23,7 @@
 // minimum folds them into a running minimum.  A block whose 16-bit minimum
 // reaches the threshold is rescanned exactly in int32, and only exact hits
 // are recorded.  Error bound of the 16-bit value x(g) of a configuration:
-//   E(g)/2^16 - 10 < x(g) - 2^15 <= E(g)/2^16 + 1,
+//   E(g)/2^16 - 11 < x(g) - 2^15 <= E(g)/2^16 + 1,
 // so x(g) <= floor((tau + 2^31) / 2^16) + 1 catches every E(g) <= tau.
 //
 // Selection: hits go to a shared-memory buffer (spill area in the
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
 
         unsigned long long cmid = 0ull;   // middle spins of the current block: gray(u) << 8
         for (unsigned u = 0; u < nblocks; ++u) {
-            // ---- one block: 256 configurations per walk, four walks
+            // ---- one block: 512 configurations per walk, four walks
             pk.Xa = pack_energy(E0[0], E0[1]);
             pk.Xb = pack_energy(E0[2], E0[3]);
             pk.M = __vminu2(pk.Xa, pk.Xb);
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
                 refresh_threshold();
             }
 
-            // ---- flip one middle spin: j = 8 + ctz(u + 1)
+            // ---- flip one middle spin: j = kInnerBits + ctz(u + 1)
             if (u + 1 < nblocks) {
                 const unsigned u1 = u + 1;
                 const int jrel = __ffs(u1) - 1;
@@ -312,11 +312,16 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
 #pragma unroll
                     for (int w = 0; w < kWalks; w++) F[w] = field_at(s, n, j, cfg0[w] | cmid);
                 }
-                const int4 c0 = *reinterpret_cast<const int4*>(&s.col[j][0]);
-                const int4 c1 = *reinterpret_cast<const int4*>(&s.col[j][4]);
-                const int4 c2 = *reinterpret_cast<const int4*>(&s.col[j][8]);
-                const int colv[kInnerBits + kKeep] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y,
-                                                      c1.z, c1.w, c2.x, c2.y, c2.z, c2.w};
+                static_assert(kInnerBits + kKeep <= 16, "column table holds 16 entries");
+                int colv[16];
+#pragma unroll
+                for (int q4 = 0; q4 < 4; q4++) {
+                    const int4 cv = *reinterpret_cast<const int4*>(&s.col[j][4 * q4]);
+                    colv[4 * q4 + 0] = cv.x;
+                    colv[4 * q4 + 1] = cv.y;
+                    colv[4 * q4 + 2] = cv.z;
+                    colv[4 * q4 + 3] = cv.w;
+                }
                 // unsigned arithmetic: exact modulo 2^32, and every true result fits in int32
 #pragma unroll
                 for (int w = 0; w < kWalks; w++) {

@@ -78,7 +78,7 @@ def test_batched_float32_uniform_n(bf, o):
     insts = [(J.astype(np.float32), h.astype(np.float32)) for J, h in
              (instances.dense_gaussian(22, 70 + i) for i in range(6))]
     args = bf.pack_batch(insts, dtype=torch.float32)
-    en, st = bf.low_spectrum_batched(*args[:5], 32, n_max=args[5], task_log2=18)
+    en, st = bf.low_spectrum_batched(*args[:5], 32, n_max=args[5], task_log2=21)
     ref = [(J.astype(np.float64), h.astype(np.float64)) for J, h in insts]
     check_all(o, ref, en.cpu().numpy(), bf.states_u64(st).reshape(en.shape), 32)
 
