@@ -38,7 +38,10 @@ constexpr int kBBuf = 2 * kInnerSteps;       // records per warp buffer (room fo
 constexpr int kBSeed = 1024;                  // sampled configurations per instance for its first threshold
 constexpr int kBSeedThreads = 256;
 constexpr size_t kBWarpSmem = (size_t)kBBuf * 12;                 // record buffer bytes per warp
-constexpr size_t kBSmem = kBWarpSmem * kBWarps + (size_t)kInnerSteps * 8;   // + the unit's tables
+constexpr int kBSyncEvery = 1;                   // unrolled blocks between block barriers
+// + the unit's tables: dT16, T (kInnerSteps each), J_q (kBMaxN^2), h_q (kBMaxN), columns (kBMaxN x 16)
+constexpr size_t kBSmem = kBWarpSmem * kBWarps + (size_t)kInnerSteps * 8 + (size_t)kBMaxN * kBMaxN * 4 +
+                          (size_t)kBMaxN * 4 + (size_t)kBMaxN * 16 * 4;
 
 __device__ __forceinline__ double load_value(const void* p, int dtype, size_t idx)
 {
@@ -392,6 +395,9 @@ __global__ void __launch_bounds__(kBThreads, 2) bwalk_kernel(const BatchParams p
     int* Ew = reinterpret_cast<int*>(Cw + kBBuf);
     unsigned* dTw = reinterpret_cast<unsigned*>(smem_raw + kBWarpSmem * kBWarps);
     int* Tw = reinterpret_cast<int*>(dTw + kInnerSteps);
+    int* Jq = Tw + kInnerSteps;                       // n x n (row stride n)
+    int* hq = Jq + kBMaxN * kBMaxN;
+    int (*colq)[16] = reinterpret_cast<int(*)[16]>(hq + kBMaxN);
     __shared__ unsigned long long s_unit;
     __shared__ int s_count[kBWarps];
     const unsigned long long total = *(volatile unsigned long long*)&p.hdr->total_units;
@@ -418,6 +424,9 @@ __global__ void __launch_bounds__(kBThreads, 2) bwalk_kernel(const BatchParams p
             dTw[i] = I->dT16[i];
             Tw[i] = I->T[i];
         }
+        for (int i = threadIdx.x; i < n * n; i += blockDim.x) Jq[i] = I->Jq[i];
+        for (int i = threadIdx.x; i < kBMaxN; i += blockDim.x) hq[i] = I->hq[i];
+        for (int i = threadIdx.x; i < kBMaxN * 16; i += blockDim.x) colq[i / 16][i % 16] = I->col[i / 16][i % 16];
         __syncthreads();
 
         // walks of this thread: tasks lu * 2^10 + threadIdx.x * 4 + w
@@ -425,32 +434,67 @@ __global__ void __launch_bounds__(kBThreads, 2) bwalk_kernel(const BatchParams p
         unsigned long long cfg0[kWalks];
         unsigned active_mask = 0;
         const int walk_shift = kInnerBits + m;
+        const unsigned long long task0 = (lu << kBUnitWalkBits) + (unsigned long long)(threadIdx.x * kWalks);
 #pragma unroll
-        for (int w = 0; w < kWalks; w++) {
-            unsigned long long task = (lu << kBUnitWalkBits) + (unsigned long long)(threadIdx.x * kWalks + w);
-            if (task < ntasks) active_mask |= 1u << w; else task = 0;
-            const unsigned long long c = task << walk_shift;
-            cfg0[w] = c;
+        for (int w = 0; w < kWalks; w++)
+            if (task0 + (unsigned long long)w < ntasks) active_mask |= 1u << w;
+        cfg0[0] = (active_mask & 1u) ? (task0 << walk_shift) : 0ull;
+        // full O(n^2) state of the first walk; the others differ from it in the two lowest task
+        // spins (walk_shift, walk_shift + 1) and are reached by O(n) flips
+        {
+            const unsigned long long c = cfg0[0];
             int e = 0;
             for (int i = 0; i < n; i++) {
-                int row = I->hq[i];
-                for (int j = i + 1; j < n; j++) row += ((c >> j) & 1ull) ? I->Jq[i * n + j] : -I->Jq[i * n + j];
+                int row = hq[i];
+                for (int j = i + 1; j < n; j++) row += ((c >> j) & 1ull) ? Jq[i * n + j] : -Jq[i * n + j];
                 e += ((c >> i) & 1ull) ? row : -row;
             }
-            E0[w] = e;
+            E0[0] = e;
 #pragma unroll
             for (int k = 0; k < kInnerBits; k++) {
-                int f = I->hq[k];
-                for (int j = kInnerBits; j < n; j++) f += ((c >> j) & 1ull) ? I->Jq[k * n + j] : -I->Jq[k * n + j];
-                G[w][k] = 2 * f;
+                int f = hq[k];
+                for (int j = kInnerBits; j < n; j++) f += ((c >> j) & 1ull) ? Jq[k * n + j] : -Jq[k * n + j];
+                G[0][k] = 2 * f;
             }
 #pragma unroll
             for (int r = 0; r < kKeep; r++) {
                 const int l = kInnerBits + r;
-                int f = l < n ? I->hq[l] : 0;
+                int f = l < n ? hq[l] : 0;
                 if (l < n)
-                    for (int j = 0; j < n; j++) f += ((c >> j) & 1ull) ? I->Jq[l * n + j] : -I->Jq[l * n + j];
-                Fm[w][r] = f;
+                    for (int j = 0; j < n; j++) f += ((c >> j) & 1ull) ? Jq[l * n + j] : -Jq[l * n + j];
+                Fm[0][r] = f;
+            }
+        }
+#pragma unroll
+        for (int w = 1; w < kWalks; w++) {
+            // walk 1 = walk 0 + task bit 0; walk 2 = walk 0 + task bit 1; walk 3 = walk 1 + task bit 1
+            const int from = (w == 3) ? 1 : 0;
+            const int j = walk_shift + ((w == 1) ? 0 : 1);
+            // an inactive walk duplicates the walk it is copied from (state and configuration)
+            cfg0[w] = ((active_mask >> w) & 1u) ? (cfg0[from] ^ (1ull << j)) : cfg0[from];
+            E0[w] = E0[from];
+#pragma unroll
+            for (int k = 0; k < kInnerBits; k++) G[w][k] = G[from][k];
+#pragma unroll
+            for (int r = 0; r < kKeep; r++) Fm[w][r] = Fm[from][r];
+            if (j < n && (active_mask >> w) & 1u) {
+                const unsigned long long c = cfg0[from];
+                int f = hq[j];                                  // local field on spin j
+                for (int i = 0; i < n; i++) f += ((c >> i) & 1ull) ? Jq[j * n + i] : -Jq[j * n + i];
+                const bool up = ((c >> j) & 1ull) == 0ull;     // new value of spin j
+                const unsigned dE = (unsigned)f << 1;
+                E0[w] = (int)((unsigned)E0[w] + (up ? dE : 0u - dE));
+#pragma unroll
+                for (int k = 0; k < kInnerBits; k++) {
+                    const unsigned d = (unsigned)Jq[k * n + j] << 2;
+                    G[w][k] = (int)((unsigned)G[w][k] + (up ? d : 0u - d));
+                }
+#pragma unroll
+                for (int r = 0; r < kKeep; r++) {
+                    const int l = kInnerBits + r;
+                    const unsigned d = l < n ? (unsigned)Jq[l * n + j] << 1 : 0u;
+                    Fm[w][r] = (int)((unsigned)Fm[w][r] + (up ? d : 0u - d));
+                }
             }
         }
         Packed pk;
@@ -532,7 +576,7 @@ __global__ void __launch_bounds__(kBThreads, 2) bwalk_kernel(const BatchParams p
                 }
             }
             if ((ub & 3u) == 3u) refresh();
-            __syncthreads();   // keep the block's warps on the same stretch of the unrolled code
+            if ((ub % kBSyncEvery) == kBSyncEvery - 1) __syncthreads();   // keep the warps on the same code
             // flip one middle spin
             if (ub + 1 < nblocks) {
                 const unsigned u1 = ub + 1;
@@ -552,14 +596,14 @@ __global__ void __launch_bounds__(kBThreads, 2) bwalk_kernel(const BatchParams p
 #pragma unroll
                     for (int w = 0; w < kWalks; w++) {
                         const unsigned long long c = cfg0[w] | cmid;
-                        int f = I->hq[j];
-                        for (int i = 0; i < n; i++) f += ((c >> i) & 1ull) ? I->Jq[j * n + i] : -I->Jq[j * n + i];
+                        int f = hq[j];
+                        for (int i = 0; i < n; i++) f += ((c >> i) & 1ull) ? Jq[j * n + i] : -Jq[j * n + i];
                         F[w] = f;
                     }
                 }
                 int colv[kInnerBits + kKeep];
 #pragma unroll
-                for (int k = 0; k < kInnerBits + kKeep; k++) colv[k] = I->col[j][k];
+                for (int k = 0; k < kInnerBits + kKeep; k++) colv[k] = colq[j][k];
 #pragma unroll
                 for (int w = 0; w < kWalks; w++) {
                     const unsigned dE = (unsigned)F[w] << 1;
