@@ -231,6 +231,20 @@ bf_status bf_last_profile(float* enumeration_ms);
 /* Number of kernels this library has launched in the process so far. */
 int64_t bf_launch_count(void);
 
+/*
+ * bf_merge_lists -- the S lowest records of k result lists (host memory).
+ * A search split across processes or GPUs by fixed_bits / fixed_value
+ * (disjoint subspaces, the chunk offset of Sec. 3, Eq. (6)) gives one sorted
+ * list per shard; the S lowest records overall are the first S of their union
+ * under the order (E, c) of Algorithm 1 (Sec. 3).
+ *   energies   host, k pointers to S_each values (int64 for BF_I32, double otherwise)
+ *   states     host, k pointers to S_each configuration integers
+ *   out_*      host, S values each
+ * A configuration listed more than once is kept once.  Pure host code.
+ */
+bf_status bf_merge_lists(int k, const void* const* energies, const uint64_t* const* states, int S_each,
+                         bf_dtype dtype, int S, void* out_energies, uint64_t* out_states);
+
 /* Human-readable name of a status code. */
 const char* bf_status_string(bf_status s);
 

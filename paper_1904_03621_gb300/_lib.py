@@ -17,7 +17,8 @@ BF_VARIANT_AUTO, BF_VARIANT_GRAY = 0, 1
 # every symbol include/bf.h declares
 EXPORTS = ["bf_workspace_size", "bf_low_spectrum", "bf_low_spectrum_noalloc", "bf_batched_workspace_size",
            "bf_low_spectrum_batched", "bf_low_spectrum_backward", "bf_workspace_status",
-           "bf_last_profile", "bf_launch_count", "bf_status_string", "bf_last_error_detail", "bf_version"]
+           "bf_last_profile", "bf_launch_count", "bf_merge_lists", "bf_status_string", "bf_last_error_detail",
+           "bf_version"]
 
 
 class Options(ctypes.Structure):
@@ -60,6 +61,8 @@ def load(path: str | None = None):
                                             ctypes.POINTER(Options), vp]
     lib.bf_low_spectrum_backward.restype = i32
     lib.bf_low_spectrum_backward.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, vp, i32, vp]
+    lib.bf_merge_lists.restype = i32
+    lib.bf_merge_lists.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(vp), i32, i32, i32, vp, vp]
     lib.bf_workspace_status.restype = i32
     lib.bf_workspace_status.argtypes = [vp, vp]
     lib.bf_status_string.restype = ctypes.c_char_p

@@ -2,6 +2,7 @@
 // launch plan, workspace layout and the kernel sequence of one search.
 #include <algorithm>
 #include <atomic>
+#include <vector>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -436,4 +437,46 @@ extern "C" bf_status bf_low_spectrum_backward(const uint64_t* states, const doub
                                         reinterpret_cast<const long long*>(h_offsets), dJ, dh,
                                         out_dtype == BF_F64 ? 1 : 0, static_cast<cudaStream_t>(stream_ptr));
     return e == cudaSuccess ? BF_OK : cuda_fail(e, "backward kernel");
+}
+
+// ---- merge of per-shard results (host) ------------------------------------------
+
+extern "C" bf_status bf_merge_lists(int k, const void* const* energies, const uint64_t* const* states, int S_each,
+                                    bf_dtype dtype, int S, void* out_energies, uint64_t* out_states)
+{
+    g_detail.clear();
+    if (k < 1 || S_each < 1 || S < 1) return fail(BF_EINVAL, "k=%d, S_each=%d, S=%d must be >= 1", k, S_each, S);
+    if ((long long)k * S_each < S) return fail(BF_EINVAL, "fewer records (%d x %d) than S=%d", k, S_each, S);
+    if (dtype != BF_I32 && dtype != BF_F32 && dtype != BF_F64) return fail(BF_EINVAL, "unknown dtype %d", dtype);
+    if (!energies || !states || !out_energies || !out_states) return fail(BF_EINVAL, "null pointer argument");
+    struct Rec { long long ie; double e; uint64_t c; };
+    std::vector<Rec> all;
+    all.reserve((size_t)k * S_each);
+    for (int l = 0; l < k; l++) {
+        if (!energies[l] || !states[l]) return fail(BF_EINVAL, "null list %d", l);
+        for (int i = 0; i < S_each; i++) {
+            Rec r{};
+            if (dtype == BF_I32) r.ie = static_cast<const long long*>(energies[l])[i];
+            else r.e = static_cast<const double*>(energies[l])[i];
+            r.c = states[l][i];
+            all.push_back(r);
+        }
+    }
+    const bool is_int = dtype == BF_I32;
+    std::sort(all.begin(), all.end(), [is_int](const Rec& a, const Rec& b) {
+        if (is_int) { if (a.ie != b.ie) return a.ie < b.ie; }
+        else if (a.e != b.e) return a.e < b.e;
+        return a.c < b.c;
+    });
+    // shards cover disjoint subspaces; a configuration listed twice is kept once
+    int w = 0;
+    for (size_t i = 0; i < all.size() && w < S; i++) {
+        if (i > 0 && all[i].c == all[i - 1].c) continue;
+        if (is_int) static_cast<long long*>(out_energies)[w] = all[i].ie;
+        else static_cast<double*>(out_energies)[w] = all[i].e;
+        out_states[w] = all[i].c;
+        w++;
+    }
+    if (w < S) return fail(BF_EINVAL, "only %d distinct records for S=%d", w, S);
+    return BF_OK;
 }
