@@ -173,6 +173,7 @@ def batched_section(api, torch, dev, steps, warmup):
     S = 10
     B = len(insts)
     configs = float(sum(2.0 ** t[0].shape[0] for t in insts))
+    tuned = api.autotune_batched(J, Jo, h, ho, n, S, n_max=n_max)      # cached for the default calls below
     ws = torch.empty(api.batched_workspace_size(B, n_max, S, torch.float64), dtype=torch.uint8, device=dev)
     en = torch.empty(B, S, dtype=torch.float64, device=dev)
     st = torch.empty(B, S, dtype=torch.int64, device=dev)
@@ -205,6 +206,7 @@ def batched_section(api, torch, dev, steps, warmup):
     out = {"workload": "batched_4096: 2048 dense (n~U{16..28}, J~N(0,1), h~N(0,0.5^2)) + 2048 Chimera "
                        "(n~U{16..28}, J=+-1, h=0), S=10, one graph-replayed launch sequence",
            "instances_per_s": B / (ms * 1e-3), "configs_per_s": configs / (ms * 1e-3), "ms_per_step": ms,
+           "autotuned": tuned,
            "steps": steps, "plain_instances_per_s": plain_ips,
            "plain_sample": f"{len(sample)} instances, one bf_low_spectrum call each",
            "speedup_vs_plain": (B / (ms * 1e-3)) / plain_ips}

@@ -195,6 +195,24 @@ bf_status bf_low_spectrum_batched(int B, const void* J_packed, const int64_t* J_
                                   void* stream);
 
 /*
+ * bf_autotune_batched -- pick the work-unit size (opt->task_log2) and the
+ * persistent grid (opt->grid_blocks) of bf_low_spectrum_batched for this
+ * batch by timing candidate launches (CUDA events on `stream`), as the
+ * paper tunes its launch configuration by measurement (Sec. 4.2).  Arguments
+ * as for bf_low_spectrum_batched; candidates whose workspace exceeds
+ * workspace_bytes are skipped (size the workspace with task_log2 = 21 to
+ * allow them all).  Writes the fastest options to *best and its time in ms to
+ * *best_ms (may be NULL) and caches them for this device and (B, n_max, S,
+ * dtype): later bf_low_spectrum_batched / bf_batched_workspace_size calls
+ * that leave task_log2 and grid_blocks at 0 use the cached choice.  Runs the
+ * batched search several times and synchronises the stream.
+ */
+bf_status bf_autotune_batched(int B, const void* J_packed, const int64_t* J_offsets, const void* h_packed,
+                              const int64_t* h_offsets, const int32_t* n, int n_max, int S, bf_dtype dtype,
+                              void* energies, uint64_t* states, void* workspace, size_t workspace_bytes,
+                              void* stream, bf_options* best, float* best_ms);
+
+/*
  * bf_low_spectrum_backward -- gradient of L = sum_b sum_k g[b,k] E_b(s^(b,k))
  * with respect to each instance's couplings and fields.  Eq. (1) (Sec. 2) is
  * linear in J and h, so dL/dJ_ij = sum_k g_k s_i s_j (i < j) and

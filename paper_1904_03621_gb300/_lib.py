@@ -16,7 +16,7 @@ BF_VARIANT_AUTO, BF_VARIANT_GRAY = 0, 1
 
 # every symbol include/bf.h declares
 EXPORTS = ["bf_workspace_size", "bf_low_spectrum", "bf_low_spectrum_noalloc", "bf_batched_workspace_size",
-           "bf_low_spectrum_batched", "bf_low_spectrum_backward", "bf_workspace_status",
+           "bf_low_spectrum_batched", "bf_autotune_batched", "bf_low_spectrum_backward", "bf_workspace_status",
            "bf_last_profile", "bf_launch_count", "bf_merge_lists", "bf_status_string", "bf_last_error_detail",
            "bf_version"]
 
@@ -59,6 +59,9 @@ def load(path: str | None = None):
     lib.bf_low_spectrum_batched.restype = i32
     lib.bf_low_spectrum_batched.argtypes = [i32, vp, vp, vp, vp, vp, i32, i32, i32, vp, vp, vp, sz,
                                             ctypes.POINTER(Options), vp]
+    lib.bf_autotune_batched.restype = i32
+    lib.bf_autotune_batched.argtypes = [i32, vp, vp, vp, vp, vp, i32, i32, i32, vp, vp, vp, sz, vp,
+                                        ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_float)]
     lib.bf_low_spectrum_backward.restype = i32
     lib.bf_low_spectrum_backward.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, vp, i32, vp]
     lib.bf_merge_lists.restype = i32

@@ -233,3 +233,27 @@ class LowSpectrumBatchedFn(torch.autograd.Function):
             g_en = torch.zeros(st.shape, dtype=torch.float64, device=st.device)
         dJ, dh = low_spectrum_backward(st, g_en, n, J_offsets, h_offsets, nj, nh)
         return dJ.to(jdt), dh.to(hdt), None, None, None, None, None
+
+
+def autotune_batched(J_packed, J_offsets, h_packed, h_offsets, n, S: int, *, n_max: int, stream=None):
+    """Time the batched search over candidate unit sizes and grids (bf_autotune_batched).
+
+    Returns {"task_log2", "grid_blocks", "ms"}; the choice is cached in the library for
+    this device and batch shape, so later calls with default options use it.
+    """
+    lib = _lib.load()
+    dt = J_packed.dtype
+    B = n.shape[0]
+    nbytes = batched_workspace_size(B, n_max, S, dt, task_log2=21)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=J_packed.device)
+    edt = torch.int64 if dt == torch.int32 else torch.float64
+    en = torch.empty(B, S, dtype=edt, device=J_packed.device)
+    st = torch.empty(B, S, dtype=torch.int64, device=J_packed.device)
+    best = _lib.Options()
+    ms = ctypes.c_float(0.0)
+    status = lib.bf_autotune_batched(B, J_packed.data_ptr(), J_offsets.data_ptr(), h_packed.data_ptr(),
+                                     h_offsets.data_ptr(), n.data_ptr(), n_max, S, _DTYPES[dt], en.data_ptr(),
+                                     st.data_ptr(), ws.data_ptr(), nbytes, _stream_handle(stream),
+                                     ctypes.byref(best), ctypes.byref(ms))
+    _lib.check(status, lib)
+    return {"task_log2": best.task_log2, "grid_blocks": best.grid_blocks, "ms": float(ms.value)}

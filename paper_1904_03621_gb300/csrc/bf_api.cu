@@ -2,6 +2,9 @@
 // launch plan, workspace layout and the kernel sequence of one search.
 #include <algorithm>
 #include <atomic>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 #include <cstdarg>
 #include <cstdio>
@@ -313,6 +316,30 @@ const char* bf_version(void) { return "libbf 0.1 (sm_103a)"; }
 
 namespace {
 
+// autotuned options per (device, B, n_max, S, dtype); used when the caller leaves
+// task_log2 and grid_blocks at 0
+using TuneKey = std::tuple<int, int, int, int, int>;
+std::mutex g_tune_mutex;
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;   // -> (task_log2, grid_blocks)
+
+bf_options effective_batched_options(int B, int n_max, int S, int dtype, const bf_options* opt)
+{
+    bf_options o{};
+    if (opt) o = *opt;
+    if (o.task_log2 == 0 && o.grid_blocks == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) {
+            std::lock_guard<std::mutex> lock(g_tune_mutex);
+            auto it = g_tune_cache.find(TuneKey{dev, B, n_max, S, dtype});
+            if (it != g_tune_cache.end()) {
+                o.task_log2 = it->second.first;
+                o.grid_blocks = it->second.second;
+            }
+        }
+    }
+    return o;
+}
+
 struct BPlan {
     int B, n_max, S, dtype, m_cap, pool_cap, final_len, grid, max_waves;
     size_t off_inst, off_tau, off_count, off_order, off_unit, off_poolE, off_poolC, total;
@@ -369,7 +396,8 @@ extern "C" {
 size_t bf_batched_workspace_size(int B, int n_max, int S, bf_dtype dtype, const bf_options* opt)
 {
     BPlan bp;
-    if (make_bplan(B, n_max, S, dtype, opt, bp) != BF_OK) return 0;
+    const bf_options o = effective_batched_options(B, n_max, S, dtype, opt);
+    if (make_bplan(B, n_max, S, dtype, &o, bp) != BF_OK) return 0;
     return bp.total;
 }
 
@@ -380,7 +408,8 @@ bf_status bf_low_spectrum_batched(int B, const void* J_packed, const int64_t* J_
 {
     g_detail.clear();
     BPlan bp;
-    bf_status st = make_bplan(B, n_max, S, dtype, opt, bp);
+    const bf_options eff = effective_batched_options(B, n_max, S, dtype, opt);
+    bf_status st = make_bplan(B, n_max, S, dtype, &eff, bp);
     if (st != BF_OK) return st;
     if (!J_packed || !J_offsets || !h_packed || !h_offsets || !n || !energies || !states || !workspace)
         return fail(BF_EINVAL, "null pointer argument");
@@ -478,5 +507,65 @@ extern "C" bf_status bf_merge_lists(int k, const void* const* energies, const ui
         w++;
     }
     if (w < S) return fail(BF_EINVAL, "only %d distinct records for S=%d", w, S);
+    return BF_OK;
+}
+
+// ---- autotuner for the batched search ---------------------------------------------
+
+extern "C" bf_status bf_autotune_batched(int B, const void* J_packed, const int64_t* J_offsets, const void* h_packed,
+                                         const int64_t* h_offsets, const int32_t* n, int n_max, int S,
+                                         bf_dtype dtype, void* energies, uint64_t* states, void* workspace,
+                                         size_t workspace_bytes, void* stream_ptr, bf_options* best,
+                                         float* best_ms)
+{
+    g_detail.clear();
+    if (!best) return fail(BF_EINVAL, "null output options");
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "device query");
+    const int bps = bf::batched_walker_blocks_per_sm();
+    cudaEvent_t t0, t1;
+    if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess)
+        return fail(BF_ECUDA, "event creation failed");
+    float best_t = 1e30f;
+    bf_options best_o{};
+    int tried = 0;
+    const int task_candidates[] = {21, 23, 25, 27};
+    for (int tl : task_candidates) {
+        for (int per_sm = 1; per_sm <= bps; per_sm++) {
+            bf_options o{};
+            o.task_log2 = tl;
+            o.grid_blocks = sms * per_sm;
+            BPlan bp;
+            if (make_bplan(B, n_max, S, dtype, &o, bp) != BF_OK) continue;
+            if (bp.total > workspace_bytes) continue;       // candidate needs a larger pool
+            // one untimed run, then one timed run of the whole batched call
+            bf_status st = bf_low_spectrum_batched(B, J_packed, J_offsets, h_packed, h_offsets, n, n_max, S, dtype,
+                                                   energies, states, workspace, workspace_bytes, &o, stream);
+            if (st != BF_OK) { cudaEventDestroy(t0); cudaEventDestroy(t1); return st; }
+            cudaEventRecord(t0, stream);
+            st = bf_low_spectrum_batched(B, J_packed, J_offsets, h_packed, h_offsets, n, n_max, S, dtype, energies,
+                                         states, workspace, workspace_bytes, &o, stream);
+            cudaEventRecord(t1, stream);
+            if (st != BF_OK) { cudaEventDestroy(t0); cudaEventDestroy(t1); return st; }
+            float ms = 0.f;
+            e = cudaEventSynchronize(t1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+            if (e != cudaSuccess) { cudaEventDestroy(t0); cudaEventDestroy(t1); return cuda_fail(e, "autotune timing"); }
+            st = bf_workspace_status(workspace, stream);
+            if (st != BF_OK) continue;                       // e.g. pool too small for this chunking
+            tried++;
+            if (ms < best_t) { best_t = ms; best_o = o; }
+        }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (!tried) return fail(BF_EWORKSPACE, "no candidate fits the workspace of %zu bytes", workspace_bytes);
+    *best = best_o;
+    if (best_ms) *best_ms = best_t;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[TuneKey{dev, B, n_max, S, (int)dtype}] = {best_o.task_log2, best_o.grid_blocks};
     return BF_OK;
 }

@@ -142,3 +142,16 @@ def test_batched_4096_sample(bf):
             assert_int_equal(en[i], st[i], en_o, st_o)
         else:
             assert_float_parity(o, J, h, en[i], st[i], en_o, st_o)
+
+
+def test_batched_autotune(bf, o):
+    """The autotuner returns one of its candidates, and later default calls (which use the
+    cached choice) give the same exact results as explicit options."""
+    insts = mixed_batch(24, 123, 16, 24)
+    args = bf.pack_batch(insts)
+    tuned = bf.autotune_batched(*args[:5], 10, n_max=args[5])
+    assert tuned["task_log2"] in (21, 23, 25, 27) and tuned["grid_blocks"] > 0 and tuned["ms"] > 0
+    en_d, st_d = bf.low_spectrum_batched(*args[:5], 10, n_max=args[5])
+    en_e, st_e = bf.low_spectrum_batched(*args[:5], 10, n_max=args[5], task_log2=25, grid_blocks=152)
+    assert np.array_equal(bf.states_u64(st_d), bf.states_u64(st_e))
+    check_all(o, insts, en_d.cpu().numpy(), bf.states_u64(st_d).reshape(en_d.shape), 10)
