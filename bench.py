@@ -250,6 +250,8 @@ def main():
     ap.add_argument("--workload", default="float_n48")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--variant", default="gray", choices=["gray", "tc"],
+                    help="screening kernel: Gray-code walk or tensor-core tiles")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -277,7 +279,8 @@ def main():
     hh = torch.from_numpy(np.ascontiguousarray(h)).pin_memory()
     Jd = torch.empty_like(Jh, device=dev)
     hd = torch.empty_like(hh, device=dev)
-    ws = torch.empty(api.workspace_size(n, S, Jh.dtype), dtype=torch.uint8, device=dev)
+    ws = torch.empty(api.workspace_size(n, S, Jh.dtype, variant={"gray": 1, "tc": 2}[args.variant]),
+                     dtype=torch.uint8, device=dev)
     edt = torch.int64 if Jh.dtype == torch.int32 else torch.float64
     en = torch.empty(S, dtype=edt, device=dev)
     st = torch.empty(S, dtype=torch.int64, device=dev)
@@ -285,6 +288,7 @@ def main():
     st_h = torch.empty(S, dtype=torch.int64).pin_memory()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
     stream = torch.cuda.current_stream()
+    variant = {"gray": 1, "tc": 2}[args.variant]
 
     def step(profile):
         Jd.copy_(Jh, non_blocking=True)
@@ -292,7 +296,7 @@ def main():
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        api.low_spectrum(Jd, hd, S, workspace=ws, out=(en, st), check=False, profile=profile)
+        api.low_spectrum(Jd, hd, S, workspace=ws, out=(en, st), check=False, profile=profile, variant=variant)
         ev1.record(stream)
         en_h.copy_(en, non_blocking=True)
         st_h.copy_(st, non_blocking=True)

@@ -66,8 +66,11 @@ typedef enum {
 /* Screening kernel choice for bf_low_spectrum. */
 typedef enum {
     BF_VARIANT_AUTO = 0,   /* library default (Gray-code walk) */
-    BF_VARIANT_GRAY = 1    /* Gray-code walk: exact int32 fixed point with a
+    BF_VARIANT_GRAY = 1,   /* Gray-code walk: exact int32 fixed point with a
                               two-lane 16-bit pre-filter, one flip per step */
+    BF_VARIANT_TC = 2      /* tensor-core screening: 128 x 256 energies per
+                              tcgen05 MMA (BF16 hi+lo splits, FP32 accumulation),
+                              exact int32 rescans; needs n - fixed_bits >= 15 */
 } bf_variant;
 
 /*

@@ -57,6 +57,7 @@ struct Plan {
     int n, S, dtype, free_bits;
     unsigned long long hiconst;
     bool direct;
+    int variant;
     int list_cap, grid, m, nh, seg_log2, seed_per_block, seed_blocks;
     unsigned long long seed_sample;
     bf::Layout L;
@@ -69,7 +70,7 @@ bf_status make_plan(int n, int S, int dtype, const bf_options* opt, Plan& pl)
     if (opt) o = *opt;
     if (n < 1 || n > bf::kMaxN) return fail(BF_EINVAL, "n=%d outside [1, 64]", n);
     if (dtype != BF_I32 && dtype != BF_F32 && dtype != BF_F64) return fail(BF_EINVAL, "unknown dtype %d", dtype);
-    if (o.variant != BF_VARIANT_AUTO && o.variant != BF_VARIANT_GRAY)
+    if (o.variant != BF_VARIANT_AUTO && o.variant != BF_VARIANT_GRAY && o.variant != BF_VARIANT_TC)
         return fail(BF_EINVAL, "unknown variant %d", o.variant);
     if (o.fixed_bits < 0 || o.fixed_bits > n) return fail(BF_EINVAL, "fixed_bits=%d outside [0, n]", o.fixed_bits);
     const int free_bits = n - o.fixed_bits;
@@ -99,18 +100,36 @@ bf_status make_plan(int n, int S, int dtype, const bf_options* opt, Plan& pl)
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(e, "device query");
     pl.list_cap = bf::list_capacity(S);
-    int bps = bf::gray_blocks_per_sm(pl.list_cap);
-    if (bps < 1) return fail(BF_ECUDA, "enumeration kernel does not fit on an SM (S=%d)", S);
-    pl.grid = o.grid_blocks ? o.grid_blocks : sms * bps;
-    const int walk_bits = free_bits - bf::kInnerBits;    // middle + task-index bits
-    if (o.task_log2) {
-        pl.m = std::min(std::max(o.task_log2 - bf::kInnerBits, 0), walk_bits);
+    pl.variant = o.variant == BF_VARIANT_TC ? BF_VARIANT_TC : BF_VARIANT_GRAY;
+    if (pl.variant == BF_VARIANT_TC) {
+        // one 256-thread block per SM (each holds all 512 TMEM columns); a task is 2^m tiles
+        if (free_bits < 15) return fail(BF_EUNSUPPORTED, "the tensor-core variant needs n - fixed_bits >= 15");
+        if (bf::tc_smem_bytes(n, pl.list_cap) > (size_t)227 * 1024)
+            return fail(BF_EUNSUPPORTED, "S=%d too large for the tensor-core variant", S);
+        pl.grid = o.grid_blocks ? o.grid_blocks : sms;
+        const int outer = free_bits - 15;
+        if (o.task_log2) {
+            pl.m = std::min(std::max(o.task_log2 - 15, 0), std::min(outer, 16));
+        } else {
+            const int tasks = ceil_log2((unsigned long long)pl.grid) + 3;
+            pl.m = std::min(std::max(outer - tasks, 0), 16);
+        }
+        pl.nh = outer - pl.m;
+        pl.seg_log2 = std::min(pl.m, 4);
     } else {
-        const int chains = ceil_log2((unsigned long long)pl.grid * bf::kGrayThreads * bf::kWalks);
-        pl.m = std::min(std::max(walk_bits - (chains + 2), 0), 14);
+        int bps = bf::gray_blocks_per_sm(pl.list_cap);
+        if (bps < 1) return fail(BF_ECUDA, "enumeration kernel does not fit on an SM (S=%d)", S);
+        pl.grid = o.grid_blocks ? o.grid_blocks : sms * bps;
+        const int walk_bits = free_bits - bf::kInnerBits;    // middle + task-index bits
+        if (o.task_log2) {
+            pl.m = std::min(std::max(o.task_log2 - bf::kInnerBits, 0), walk_bits);
+        } else {
+            const int chains = ceil_log2((unsigned long long)pl.grid * bf::kGrayThreads * bf::kWalks);
+            pl.m = std::min(std::max(walk_bits - (chains + 2), 0), 14);
+        }
+        pl.nh = walk_bits - pl.m;
+        pl.seg_log2 = std::min(pl.m, 4);
     }
-    pl.nh = walk_bits - pl.m;
-    pl.seg_log2 = std::min(pl.m, 4);
     // seed: a pseudo-random sample of up to 2^20 configurations, one sorted list per block
     pl.seed_per_block = std::max(pl.list_cap, 2048);
     unsigned long long sample = 1ull << std::min(free_bits, bf::kSeedLog2);
@@ -184,6 +203,8 @@ bf_status bf_low_spectrum(const void* J, const void* h, int n, int S, bf_dtype d
     pp.S = S;
     pp.free_bits = pl.free_bits;
     pp.hiconst = pl.hiconst;
+    // the tensor-core variant needs 4x headroom: its cross coefficients reach 4 sum|J|
+    pp.emq_log2 = pl.variant == BF_VARIANT_TC ? bf::kEmqLog2 - 2 : bf::kEmqLog2;
     pp.prep = prep;
     pp.hdr = hdr;
     cudaError_t e = bf::launch_prep(pp, stream);
@@ -243,7 +264,31 @@ bf_status bf_low_spectrum(const void* J, const void* h, int n, int S, bf_dtype d
         e = cudaEventRecord(g_prof.start, stream);
         if (e != cudaSuccess) return cuda_fail(e, "profile event");
     }
-    e = bf::launch_gray(gp, pl.grid, stream);
+    if (pl.variant == BF_VARIANT_TC) {
+        bf::TcParams tp{};
+        tp.n = n;
+        tp.m = pl.m;
+        tp.nh = pl.nh;
+        tp.free_bits = pl.free_bits;
+        tp.hiconst = pl.hiconst;
+        tp.ntasks = 1ull << pl.nh;
+        tp.S = S;
+        tp.list_cap = L.list_cap;
+        tp.W = hl.W;
+        tp.seg_log2 = pl.seg_log2;
+        tp.spill_cap = L.spill_cap;
+        // split residuals <= 2^-18 |x| for 8 values below 2^30, FP32 accumulation and conversions
+        tp.delta = 1 << 17;
+        tp.prep = prep;
+        tp.hdr = hdr;
+        tp.list_E = AE;
+        tp.list_C = AC;
+        tp.spill_E = gp.spill_E;
+        tp.spill_C = gp.spill_C;
+        e = bf::launch_tc(tp, pl.grid, stream);
+    } else {
+        e = bf::launch_gray(gp, pl.grid, stream);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "enumeration kernel");
     if (profile) {
         e = cudaEventRecord(g_prof.stop, stream);

@@ -152,10 +152,24 @@ struct PrepParams {
     const void* h;
     int n, dtype, S, free_bits;
     unsigned long long hiconst;
-    int seed_count;
+    int emq_log2;                   // |E_q| and |local fields| < 2^emq_log2
     int pad0;
     Prep* prep;
     WsHeader* hdr;
+};
+
+struct TcParams {                   // tensor-core screening kernel (k_tc.cu)
+    int n, m, nh, free_bits;        // m walked outer spins per task, nh task-index bits
+    unsigned long long hiconst, ntasks;
+    int S, list_cap, W, seg_log2;
+    unsigned spill_cap;
+    int delta;                      // widening of the tensor-core test (quantised units)
+    const Prep* prep;
+    WsHeader* hdr;
+    int* list_E;
+    unsigned long long* list_C;
+    int* spill_E;
+    unsigned long long* spill_C;
 };
 
 // ---- batched search ----------------------------------------------------
@@ -210,6 +224,8 @@ bf_status report(bf_status s, const char* detail);
 
 cudaError_t launch_prep(const PrepParams& p, cudaStream_t s);
 cudaError_t launch_gray(const GrayParams& p, int grid, cudaStream_t s);
+cudaError_t launch_tc(const TcParams& p, int grid, cudaStream_t s);
+size_t tc_smem_bytes(int n, int list_cap);
 int gray_blocks_per_sm(int list_cap);
 size_t gray_smem_bytes(int n, int list_cap);
 

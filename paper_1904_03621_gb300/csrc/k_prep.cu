@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(const PrepParams p)
         if (emax > 0.0) {
             int e;
             frexp(emax, &e);            // emax < 2^e
-            q = kEmqLog2 - e;
+            q = p.emq_log2 - e;
             if (p.dtype == 0) {
                 if (q < 0) status |= kErrRange;  // integer instance too large for int32 fixed point
                 if (q > 16) q = 16;              // integers: 16-bit filter lane = 1 energy unit
