@@ -21,20 +21,28 @@ __device__ __forceinline__ void cmp_swap(K* key, unsigned long long* cfg, int lo
     }
 }
 
-// Sort len (a power of two) records.
-template <typename K>
-__device__ void block_sort(K* key, unsigned long long* cfg, int len)
+// Sort len (a power of two) records with the nt threads t = 0 .. nt-1 of a
+// group that synchronises with sync().
+template <typename K, typename Sync>
+__device__ void group_sort(K* key, unsigned long long* cfg, int len, int t, int nt, Sync sync)
 {
     for (int size = 2; size <= len; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            __syncthreads();
-            for (int i = threadIdx.x; i < (len >> 1); i += blockDim.x) {
+            sync();
+            for (int i = t; i < (len >> 1); i += nt) {
                 int lo = 2 * stride * (i / stride) + (i % stride);
                 cmp_swap(key, cfg, lo, lo + stride, (lo & size) == 0);
             }
         }
     }
-    __syncthreads();
+    sync();
+}
+
+// Sort len (a power of two) records with the whole block.
+template <typename K>
+__device__ void block_sort(K* key, unsigned long long* cfg, int len)
+{
+    group_sort(key, cfg, len, (int)threadIdx.x, (int)blockDim.x, [] { __syncthreads(); });
 }
 
 // Merge two sorted halves [0, len/2) and [len/2, len) (len a power of two).

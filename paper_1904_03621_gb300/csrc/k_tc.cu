@@ -1,5 +1,5 @@
 // Tensor-core screening (step A2): energies of 128 x 256 configurations per
-// tcgen05.mma, threshold test on the accumulator in TMEM.
+// tcgen05.mma, reduced to one minimum per TMEM lane by the loading unit.
 //
 // Spin roles in a configuration c (bit i = spin i):
 //   R = spins [0, 7)    rows of a tile (128 patterns, q_i = bit i of the row)
@@ -21,9 +21,25 @@
 // dR(r) + delta; delta bounds the split residuals (<= 2^-17 |x| each), the FP32
 // accumulation and the conversions (values are below 2^31 in magnitude).  A
 // flagged row is rescanned exactly in int32 and only exact hits are recorded.
-// Per outer flip j: E_base += 2 s_j F_j, dR(r) += 4 s_j GR_j(r), dQ(c) += 4 s_j GC_j(c)
-// with table lookups; the next tile's MMA is issued before the current tile's
-// epilogue (two TMEM accumulators, two B buffers).
+// Per outer flip l: E_base += 2 s_l F_l, dR(r) += 4 s_l GR_l(r), dQ(c) += 4 s_l GC_l(c).
+//
+// Block = 8 epilogue warps + 2 MMA warps, no block-wide barrier inside a task:
+//   * two TMEM accumulators (stages) of 256 columns, four B operands and four
+//     row-base entries (tile t uses slot t mod 4);
+//   * MMA warp s owns the tiles of stage s.  It follows the Gray walk of the
+//     outer spins (E_base, the walked fields, 8 column terms and 4 row terms
+//     per lane), waits `ready[s]`, issues the MMA, commits it to `full[s]` and
+//     arrives on `full[s]` itself, then writes the dQ column of B and the row
+//     bases E_base + dR(r) of its next tile (two ahead).  One committing
+//     thread per stage: the commits of one thread complete in order, two
+//     threads overlap;
+//   * an epilogue warp waits `full[s]` (MMA done and its inputs published),
+//     reads its row base, reads its 32 lanes x 128 columns with four
+//     tcgen05.ld.red (minimum per lane) and arrives on `ready[s]`;
+//   * candidate lists are merged every 2^seg tiles under a named barrier of
+//     the epilogue warps only.
+// Every wait is bounded; on a timeout the block stops issuing, flags
+// kErrTimeout, waits for its last MMAs and frees its TMEM.
 #include <climits>
 #include <cuda_bf16.h>
 
@@ -33,7 +49,10 @@
 namespace bf {
 namespace {
 
-constexpr int kTcThreads = 512;                          // 16 warps: 4 per TMEM lane group
+constexpr int kTcEpWarps = 8;                            // epilogue / operand warps
+constexpr int kTcEpThreads = 32 * kTcEpWarps;            // 256
+constexpr int kTcThreads = kTcEpThreads + 64;            // + one MMA warp per stage
+constexpr int kTcBBufs = 4;                              // B operands in flight
 constexpr int kTcRowBits = 7, kTcColBits = 8;
 constexpr int kTcRows = 1 << kTcRowBits, kTcCols = 1 << kTcColBits;
 constexpr int kTcSpins = kTcRowBits + kTcColBits;        // 15
@@ -72,87 +91,56 @@ __device__ __forceinline__ unsigned long long globaltimer()
 // bounded wait for phase `parity` of an mbarrier; false after kTcWaitNs
 __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity)
 {
+    uint32_t done;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(done) : "r"(addr), "r"(parity) : "memory");
+    if (done) return true;
     const unsigned long long t0 = globaltimer();
     for (;;) {
-        uint32_t done;
         asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(done) : "r"(addr), "r"(parity));
+                     "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(done) : "r"(addr), "r"(parity) : "memory");
         if (done) return true;
         if ((long long)(globaltimer() - t0) > kTcWaitNs) return false;
     }
 }
 
-__device__ __forceinline__ float min3(float a, float b, float c)
+__device__ __forceinline__ void mbar_arrive(uint32_t addr)
 {
-    float d;
-    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
-    return d;
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" :: "r"(addr) : "memory");
 }
 
-// minimum of 64 consecutive accumulator columns of this thread's TMEM lane (one load, one wait)
-__device__ __forceinline__ float tmem_min64(uint32_t taddr)
+// named barrier of the epilogue warps (the MMA warp does not take part)
+__device__ __forceinline__ void ep_sync() { asm volatile("bar.sync 1, %0;" :: "n"(kTcEpThreads) : "memory"); }
+
+__device__ __forceinline__ float tmem_min128(uint32_t taddr)
 {
-    uint32_t r[64];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x64.b32 "
-                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
-                 "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
-                 "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]),
-                   "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]),
-                   "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]),
-                   "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]),
-                   "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    // 3-input minimum tree over 64 values: 21 + 7 + 2 + 1 instructions (+1)
-    float a[22];
-#pragma unroll
-    for (int i = 0; i < 21; i++)
-        a[i] = min3(__uint_as_float(r[3 * i]), __uint_as_float(r[3 * i + 1]), __uint_as_float(r[3 * i + 2]));
-    a[21] = __uint_as_float(r[63]);
-    float b[8];
-#pragma unroll
-    for (int i = 0; i < 7; i++) b[i] = min3(a[3 * i], a[3 * i + 1], a[3 * i + 2]);
-    b[7] = a[21];
-    return min3(min3(b[0], b[1], b[2]), min3(b[3], b[4], b[5]), fminf(b[6], b[7]));
+    float m0, m1, m2, m3;
+    asm volatile("{\n\t.reg .b32 t<128>;\n\t"
+                 "tcgen05.ld.red.sync.aligned.32x32b.x32.min.f32 {t0,t1,t2,t3,t4,t5,t6,t7,t8,t9,t10,t11,t12,t13,t14,t15,t16,t17,t18,t19,t20,t21,t22,t23,t24,t25,t26,t27,t28,t29,t30,t31}, %0, [%4];\n\t"
+                 "tcgen05.ld.red.sync.aligned.32x32b.x32.min.f32 {t32,t33,t34,t35,t36,t37,t38,t39,t40,t41,t42,t43,t44,t45,t46,t47,t48,t49,t50,t51,t52,t53,t54,t55,t56,t57,t58,t59,t60,t61,t62,t63}, %1, [%5];\n\t"
+                 "tcgen05.ld.red.sync.aligned.32x32b.x32.min.f32 {t64,t65,t66,t67,t68,t69,t70,t71,t72,t73,t74,t75,t76,t77,t78,t79,t80,t81,t82,t83,t84,t85,t86,t87,t88,t89,t90,t91,t92,t93,t94,t95}, %2, [%6];\n\t"
+                 "tcgen05.ld.red.sync.aligned.32x32b.x32.min.f32 {t96,t97,t98,t99,t100,t101,t102,t103,t104,t105,t106,t107,t108,t109,t110,t111,t112,t113,t114,t115,t116,t117,t118,t119,t120,t121,t122,t123,t124,t125,t126,t127}, %3, [%7];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;\n\t}"
+                 : "=f"(m0), "=f"(m1), "=f"(m2), "=f"(m3)
+                 : "r"(taddr), "r"(taddr + 32u), "r"(taddr + 64u), "r"(taddr + 96u)
+                 : "memory");
+    return fminf(fminf(m0, m1), fminf(m2, m3));
 }
 
 struct TcSm {
     uint16_t* A;            // 128 x 16 BF16 (K-major tile)
-    uint16_t* B[2];         // 256 x 16 BF16 each
+    uint16_t* B[kTcBBufs];  // 256 x 16 BF16 each
     int* Bint;              // [7][256] integer cross coefficients
     int* GR;                // [m][128]
     int* GC;                // [m][256]
-    int* dQ;                // [3][256] column terms of the last three tiles
-    int* Fo;                // [2][kTcMaxWalk] fields of the walked outer spins
+    int* dQ0;               // [2][256] column terms of the task's first tile (one copy per MMA warp)
+    int* base;              // [4][128] E_base + dR(r) of the tiles in flight
+    int* JW;                // [kTcMaxWalk][kTcMaxWalk] JW[l][l'] = J between walked spins l and l'
     int* Jq;                // n x n
     int* hq;                // kMaxN
     int* E;                 // 2 * cap
     unsigned long long* C;  // 2 * cap
 };
-
-__device__ __forceinline__ void tc_record(const TcParams& p, const TcSm& s, unsigned* buf_count, int e,
-                                          unsigned long long c)
-{
-    unsigned slot = atomicAdd(buf_count, 1u);
-    if (slot < (unsigned)p.list_cap) {
-        s.E[p.list_cap + slot] = e;
-        s.C[p.list_cap + slot] = c;
-        return;
-    }
-    unsigned g = atomicAdd(&p.hdr->spill_count, 1u);
-    if (g < p.spill_cap) {
-        p.spill_E[g] = e;
-        p.spill_C[g] = c;
-    } else {
-        atomicOr(&p.hdr->status, kErrSpill);
-    }
-}
 
 __device__ __forceinline__ int field_of(const TcSm& s, int n, int j, unsigned long long cfg)
 {
@@ -160,6 +148,62 @@ __device__ __forceinline__ int field_of(const TcSm& s, int n, int j, unsigned lo
     for (int i = 0; i < n; i++) f += ((cfg >> i) & 1ull) ? s.Jq[j * n + i] : -s.Jq[j * n + i];
     return f;
 }
+
+// Exact rescan of one flagged row: the 128 columns [128 half, 128 half + 128)
+// of the tile whose walked spins at +1 are the bits of g.  The column term of
+// that tile is rebuilt from the task's first tile, dQ(c) = dQ0(c) + 4 sum_j
+// q_j(c) sum_{l in g} J_{7+j,15+l}, so that only data written before the
+// task's first barrier is read.
+__device__ __noinline__ void tc_rescan(const TcParams& p, const int* Jq, const int* dQ0, const int* Bint, int* E,
+                                       unsigned long long* C, unsigned* buf_count, int row, int half, unsigned base,
+                                       unsigned g, unsigned long long c0, int tau_scr, int tie_E,
+                                       unsigned long long tie_C)
+{
+    const int n = p.n, m = p.m;
+    unsigned w4[kTcColBits];
+#pragma unroll
+    for (int j = 0; j < kTcColBits; j++) {
+        unsigned a = 0u;
+        for (int l = 0; l < m; l++)
+            if ((g >> l) & 1u) a += (unsigned)Jq[(kTcRowBits + j) * n + kTcSpins + l];
+        w4[j] = a << 2;
+    }
+    const unsigned long long cb = c0 | ((unsigned long long)g << kTcSpins) | (unsigned long long)row;
+    for (int cc = 0; cc < 128; cc++) {
+        const int c = 128 * half + cc;
+        unsigned acc = base + (unsigned)dQ0[c];
+#pragma unroll
+        for (int j = 0; j < kTcColBits; j++) acc += ((c >> j) & 1) ? w4[j] : 0u;
+#pragma unroll
+        for (int i = 0; i < kTcRowBits; i++) acc += ((row >> i) & 1) ? (unsigned)Bint[i * kTcCols + c] : 0u;
+        const int e = (int)acc;
+        const unsigned long long cfg = cb | ((unsigned long long)c << kTcRowBits);
+        if (e <= tau_scr && !(e == tie_E && cfg > tie_C)) {
+            const unsigned slot = atomicAdd(buf_count, 1u);
+            if (slot < (unsigned)p.list_cap) {
+                E[p.list_cap + slot] = e;
+                C[p.list_cap + slot] = cfg;
+                continue;
+            }
+            const unsigned gs = atomicAdd(&p.hdr->spill_count, 1u);
+            if (gs < p.spill_cap) {
+                p.spill_E[gs] = e;
+                p.spill_C[gs] = cfg;
+            } else {
+                atomicOr(&p.hdr->status, kErrSpill);
+            }
+        }
+    }
+}
+
+// Gray step into tile v >= 1 of a task: walked spin l flips, up = it goes to +1
+__device__ __forceinline__ void gray_step(unsigned v, int& l, bool& up)
+{
+    l = __ffs(v) - 1;
+    up = (((v ^ (v >> 1)) >> l) & 1u) != 0u;
+}
+
+__device__ __forceinline__ unsigned addsub(unsigned x, unsigned d, bool up) { return up ? x + d : x - d; }
 
 }  // namespace
 
@@ -170,29 +214,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant
     TcSm s;
     unsigned char* q = smem_raw;
     s.A = reinterpret_cast<uint16_t*>(q);            q += kTcRows * 16 * 2;
-    s.B[0] = reinterpret_cast<uint16_t*>(q);         q += kTcCols * 16 * 2;
-    s.B[1] = reinterpret_cast<uint16_t*>(q);         q += kTcCols * 16 * 2;
+    for (int b = 0; b < kTcBBufs; b++) {
+        s.B[b] = reinterpret_cast<uint16_t*>(q);
+        q += kTcCols * 16 * 2;
+    }
     s.C = reinterpret_cast<unsigned long long*>(q);  q += (size_t)2 * cap * 8;
     s.E = reinterpret_cast<int*>(q);                 q += (size_t)2 * cap * 4;
     s.Bint = reinterpret_cast<int*>(q);              q += kTcRowBits * kTcCols * 4;
     s.GR = reinterpret_cast<int*>(q);                q += kTcMaxWalk * kTcRows * 4;
     s.GC = reinterpret_cast<int*>(q);                q += kTcMaxWalk * kTcCols * 4;
-    s.dQ = reinterpret_cast<int*>(q);                q += 3 * kTcCols * 4;
-    s.Fo = reinterpret_cast<int*>(q);                q += 2 * kTcMaxWalk * 4;
+    s.dQ0 = reinterpret_cast<int*>(q);               q += 2 * kTcCols * 4;
+    s.base = reinterpret_cast<int*>(q);              q += kTcBBufs * kTcRows * 4;
+    s.JW = reinterpret_cast<int*>(q);                q += kTcMaxWalk * kTcMaxWalk * 4;
     s.hq = reinterpret_cast<int*>(q);                q += kMaxN * 4;
     s.Jq = reinterpret_cast<int*>(q);
 
-    __shared__ __align__(8) unsigned long long mbar[2];
+    __shared__ __align__(8) unsigned long long full_bar[2], ready_bar[2];
     __shared__ uint32_t s_tmem;
     __shared__ unsigned s_buf_count;
     __shared__ int s_list_count, s_kE, s_abort;
     __shared__ unsigned long long s_kC, s_task;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int row = 32 * (warp & 3) + lane;        // TMEM lane of this thread
-    const int quarter = warp >> 2;                 // accumulator columns [64 quarter, 64 quarter + 64)
-    const bool owns_col = tid < kTcCols;           // threads 0..255 maintain one column term each
-    const int col = tid & (kTcCols - 1);
     const Prep* prep = p.prep;
 
     for (int i = tid; i < n * n; i += blockDim.x) s.Jq[i] = prep->Jq[i];
@@ -212,7 +255,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant
         b *= 4;
         s.Bint[i * kTcCols + c] = b;
         const uint32_t pr = split_bf16(b);
-        for (int bb = 0; bb < 2; bb++) {
+        for (int bb = 0; bb < kTcBBufs; bb++) {
             s.B[bb][tile_off(c, 2 * i) >> 1] = (uint16_t)(pr & 0xffffu);
             s.B[bb][tile_off(c, 2 * i + 1) >> 1] = (uint16_t)(pr >> 16);
         }
@@ -232,13 +275,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant
             if ((c >> j) & 1) g += s.Jq[(kTcRowBits + j) * n + kTcSpins + l];
         s.GC[l * kTcCols + c] = g;
     }
+    for (int idx = tid; idx < kTcMaxWalk * kTcMaxWalk; idx += blockDim.x) {
+        const int l = idx / kTcMaxWalk, l2 = idx % kTcMaxWalk;
+        s.JW[idx] = (l < m && l2 < m) ? s.Jq[(kTcSpins + l) * n + kTcSpins + l2] : 0;
+    }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" :: "r"(smem_u32(&s_tmem)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[1])));
+        for (int b = 0; b < 2; b++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 2;" :: "r"(smem_u32(&full_bar[b])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&ready_bar[b])), "n"(kTcEpWarps));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_buf_count = 0u;
         s_list_count = 0;
         s_kE = kEmptyE;
@@ -250,16 +300,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = s_tmem;
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcCols >> 3) << 17) |
-                           ((uint32_t)(kTcRows >> 4) << 24);
-    const uint64_t adesc = make_desc(smem_u32(s.A));
-    const uint64_t bdesc0 = make_desc(smem_u32(s.B[0])), bdesc1 = make_desc(smem_u32(s.B[1]));
-    uint32_t phase0 = 0u, phase1 = 0u;
-    unsigned char* const Bb0 = reinterpret_cast<unsigned char*>(s.B[0]);
-    unsigned char* const Bb1 = reinterpret_cast<unsigned char*>(s.B[1]);
-    bool aborted = false;
 
     const int S = p.S, W = p.W;
+    const int walk_shift = kTcSpins + m;
+    const unsigned ntiles = 1u << m;
+    const unsigned seg_mask = (1u << p.seg_log2) - 1u;
+    const float delta = (float)p.delta;
+    unsigned it0 = 0u;                 // global index of the task's first tile in this block
+    bool aborted = false;
+
+    // MMA warp state
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcCols >> 3) << 17) |
+                           ((uint32_t)(kTcRows >> 4) << 24);
+    long long last_issued = -1;        // last tile this MMA warp issued
+    unsigned rph = 0u;                 // phases of ready[s] this MMA warp has waited for
+
+    // epilogue warp state
+    const int row = 32 * (warp & 3) + lane;        // TMEM lane of this thread
+    const int half = (warp >> 2) & 1;              // accumulator columns [128 half, 128 half + 128)
     int tau_scr = 0, tie_E = kEmptyE;
     unsigned long long tie_C = kEmptyC;
     auto refresh = [&]() {
@@ -270,136 +328,185 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant
         tie_E = (W == 0) ? s_kE : kEmptyE;
         tie_C = s_kC;
     };
-    refresh();
-    auto issue = [&](int b) {
-        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-                     :: "r"(tmem + (uint32_t)(b * kTcCols)), "l"(adesc), "l"(b ? bdesc1 : bdesc0), "r"(idesc), "r"(0));
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                     :: "r"(smem_u32(&mbar[b])));
-    };
-
-    const int walk_shift = kTcSpins + m;
-    const unsigned ntiles = 1u << m;
-    const unsigned seg_mask = (1u << p.seg_log2) - 1u;
-    const float delta = (float)p.delta;
 
     for (;;) {
         if (tid == 0) s_task = atomicAdd(&p.hdr->task_next, 1ull);
         __syncthreads();
         const unsigned long long task = s_task;
-        if (task >= p.ntasks || s_abort) break;
-        const unsigned long long c0 = p.hiconst | (task << walk_shift);
-        // exact state of the task's first tile (walked spins, R and C all at -1)
-        int Eb = 0;
-        for (int i = 0; i < n; i++) {
-            int rw = s.hq[i];
-            for (int j = i + 1; j < n; j++) rw += ((c0 >> j) & 1ull) ? s.Jq[i * n + j] : -s.Jq[i * n + j];
-            Eb += ((c0 >> i) & 1ull) ? rw : -rw;
-        }
-        int dR = 0;       // row term of this thread's row
-        for (int i = 0; i < kTcRowBits; i++) {
-            if (!((row >> i) & 1)) continue;
-            dR += 2 * field_of(s, n, i, c0);
-            for (int i2 = i + 1; i2 < kTcRowBits; i2++)
-                if ((row >> i2) & 1) dR += 4 * s.Jq[i * n + i2];
-        }
-        int dQ = 0;       // column term of this thread's column
-        for (int j = 0; j < kTcColBits; j++) {
-            if (!((col >> j) & 1)) continue;
-            dQ += 2 * field_of(s, n, kTcRowBits + j, c0);
-            for (int j2 = j + 1; j2 < kTcColBits; j2++)
-                if ((col >> j2) & 1) dQ += 4 * s.Jq[(kTcRowBits + j) * n + kTcRowBits + j2];
-        }
-        if (tid < m) s.Fo[tid] = field_of(s, n, kTcSpins + tid, c0);
-        if (owns_col) {
-            s.dQ[col] = dQ;
-            *reinterpret_cast<uint32_t*>(Bb0 + tile_off(col, 14)) = split_bf16(dQ);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        const bool stop = task >= p.ntasks || s_abort;
         __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (tid == 0 && !aborted) issue(0);
+        if (stop) break;
+        const unsigned long long c0 = p.hiconst | (task << walk_shift);
 
-        unsigned long long cmid = 0ull;   // walked outer spins of the current tile: gray(u) << 15
-        for (unsigned u = 0; u < ntiles; ++u) {
-            const int b = u & 1;
-            int Eb_n = Eb, dR_n = dR, dQ_n = dQ;
-            // ---- prepare and issue tile u + 1
-            if (u + 1 < ntiles) {
-                const unsigned u1 = u + 1;
-                const int j = __ffs(u1) - 1;
-                const bool up = ((u1 ^ (u1 >> 1)) >> j) & 1u;
-                const int Fj = s.Fo[b * kTcMaxWalk + j];
-                Eb_n = (int)((unsigned)Eb + (up ? (unsigned)Fj << 1 : 0u - ((unsigned)Fj << 1)));
-                const unsigned gr = (unsigned)s.GR[j * kTcRows + row] << 2;
-                dR_n = (int)((unsigned)dR + (up ? gr : 0u - gr));
-                const unsigned gc = (unsigned)s.GC[j * kTcCols + col] << 2;
-                dQ_n = (int)((unsigned)dQ + (up ? gc : 0u - gc));
-                if (tid < m) {
-                    const unsigned d = (unsigned)s.Jq[(kTcSpins + tid) * n + kTcSpins + j] << 1;
-                    s.Fo[(b ^ 1) * kTcMaxWalk + tid] = (int)((unsigned)s.Fo[b * kTcMaxWalk + tid] + (up ? d : 0u - d));
-                }
-                if (owns_col) {
-                    s.dQ[((u + 1) % 3) * kTcCols + col] = dQ_n;
-                    *reinterpret_cast<uint32_t*>((b ? Bb0 : Bb1) + tile_off(col, 14)) = split_bf16(dQ_n);
-                }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                __syncthreads();
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                if (tid == 0 && !aborted) issue(b ^ 1);
+        if (warp >= kTcEpWarps) {
+            // ---------------- MMA warp mst: Gray walk of the outer spins, operands and issue of stage mst
+            const unsigned mst = (unsigned)(warp - kTcEpWarps);
+            // exact energy of the task's first tile (R, C and walked spins at -1)
+            int part = 0;
+            for (int i = lane; i < n; i += 32) {
+                int rw = s.hq[i];
+                for (int j = i + 1; j < n; j++) rw += ((c0 >> j) & 1ull) ? s.Jq[i * n + j] : -s.Jq[i * n + j];
+                part += ((c0 >> i) & 1ull) ? rw : -rw;
             }
-            // ---- epilogue of tile u
-            bool ok = !aborted && mbar_wait(smem_u32(&mbar[b]), b ? phase1 : phase0);
-            if (b) phase1 ^= 1u; else phase0 ^= 1u;
-            if (!ok && !aborted) {
-                aborted = true;
-                s_abort = 1;
-                atomicOr(&p.hdr->status, kErrTimeout);
-            }
-            if (ok) {
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(b * kTcCols + 64 * quarter);
-                const float mn = tmem_min64(ta);
-                const float thr = (float)((long long)tau_scr - (long long)Eb - (long long)dR) + delta;
-                if (mn <= thr) {
-                    // exact rescan of this thread's row and 64 columns
-                    const int* dQt = s.dQ + (u % 3) * kTcCols;
-                    const unsigned long long cb = c0 | cmid | (unsigned long long)row;
-                    const unsigned base = (unsigned)Eb + (unsigned)dR;
-                    for (int cc = 0; cc < 64; cc++) {
-                        const int c = 64 * quarter + cc;
-                        unsigned acc = base + (unsigned)dQt[c];
 #pragma unroll
-                        for (int i = 0; i < kTcRowBits; i++)
-                            acc += ((row >> i) & 1) ? (unsigned)s.Bint[i * kTcCols + c] : 0u;
-                        const int e = (int)acc;
-                        const unsigned long long cfg = cb | ((unsigned long long)c << kTcRowBits);
-                        if (e <= tau_scr && !(e == tie_E && cfg > tie_C)) tc_record(p, s, &s_buf_count, e, cfg);
+            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            int Eb = part;
+            int Fo = lane < m ? field_of(s, n, kTcSpins + lane, c0) : 0;   // field of walked spin `lane`
+            const int Fi = lane < kTcSpins ? field_of(s, n, lane, c0) : 0;  // field of tile spin `lane`
+            int F[kTcSpins];
+#pragma unroll
+            for (int i = 0; i < kTcSpins; i++) F[i] = __shfl_sync(0xffffffffu, Fi, i);
+            int dQ[kTcCols / 32], dR[kTcRows / 32];  // terms of columns / rows lane + 32 k
+#pragma unroll
+            for (int k = 0; k < kTcCols / 32; k++) {
+                const int c = lane + 32 * k;
+                int v = 0;
+#pragma unroll
+                for (int j = 0; j < kTcColBits; j++) {
+                    if (!((c >> j) & 1)) continue;
+                    v += 2 * F[kTcRowBits + j];
+                    for (int j2 = j + 1; j2 < kTcColBits; j2++)
+                        if ((c >> j2) & 1) v += 4 * s.Jq[(kTcRowBits + j) * n + kTcRowBits + j2];
+                }
+                dQ[k] = v;
+                s.dQ0[mst * kTcCols + c] = v;
+            }
+#pragma unroll
+            for (int k = 0; k < kTcRows / 32; k++) {
+                const int r = lane + 32 * k;
+                int v = 0;
+#pragma unroll
+                for (int i = 0; i < kTcRowBits; i++) {
+                    if (!((r >> i) & 1)) continue;
+                    v += 2 * F[i];
+                    for (int i2 = i + 1; i2 < kTcRowBits; i2++)
+                        if ((r >> i2) & 1) v += 4 * s.Jq[i * n + i2];
+                }
+                dR[k] = v;
+            }
+            // one step of the walk into tile v of the task
+            auto step = [&](unsigned v) {
+                int l; bool up;
+                gray_step(v, l, up);
+                const int Fl = __shfl_sync(0xffffffffu, Fo, l);
+                Eb = (int)addsub((unsigned)Eb, (unsigned)Fl << 1, up);
+                Fo = (int)addsub((unsigned)Fo, (unsigned)s.JW[l * kTcMaxWalk + (lane & (kTcMaxWalk - 1))] << 1, up);
+#pragma unroll
+                for (int k = 0; k < kTcCols / 32; k++)
+                    dQ[k] = (int)addsub((unsigned)dQ[k], (unsigned)s.GC[l * kTcCols + lane + 32 * k] << 2, up);
+#pragma unroll
+                for (int k = 0; k < kTcRows / 32; k++)
+                    dR[k] = (int)addsub((unsigned)dR[k], (unsigned)s.GR[l * kTcRows + lane + 32 * k] << 2, up);
+            };
+            // operand column and row bases of the tile in slot `slot`
+            auto publish = [&](unsigned slot) {
+                unsigned char* Bb = reinterpret_cast<unsigned char*>(s.B[slot]);
+#pragma unroll
+                for (int k = 0; k < kTcCols / 32; k++)
+                    *reinterpret_cast<uint32_t*>(Bb + tile_off(lane + 32 * k, 14)) = split_bf16(dQ[k]);
+#pragma unroll
+                for (int k = 0; k < kTcRows / 32; k++)
+                    s.base[slot * kTcRows + lane + 32 * k] = (int)((unsigned)Eb + (unsigned)dR[k]);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            };
+            unsigned u = (mst - it0) & 1u;             // first tile of this stage in the task
+            if (u < ntiles) {
+                if (u == 1u) step(1u);
+                publish((it0 + u) & (kTcBBufs - 1));
+            }
+            __syncwarp();
+            bool first = true;
+            const uint64_t adesc = make_desc(smem_u32(s.A));
+            const uint32_t bsm0 = smem_u32(s.B[0]), bstride = smem_u32(s.B[1]) - bsm0;
+            for (; u < ntiles; u += 2u) {
+                const unsigned it = it0 + u;
+                if (!aborted) aborted = __any_sync(0xffffffffu, *(volatile int*)&s_abort != 0);
+                if (aborted) break;
+                const bool more = u + 2u < ntiles;
+                if (!first) {
+                    // TMEM stage drained by the epilogue (tile u - 2)
+                    const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&ready_bar[mst]), rph & 1u));
+                    rph++;
+                    if (!ok) {
+                        aborted = true;
+                        if (lane == 0) {
+                            s_abort = 1;
+                            atomicOr(&p.hdr->status, kErrTimeout);
+                        }
+                        break;
                     }
                 }
+                first = false;
+                if (lane == 0) {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint64_t bd = make_desc(bsm0 + (it & (kTcBBufs - 1)) * bstride);
+                    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                                 :: "r"(tmem + mst * (uint32_t)kTcCols), "l"(adesc), "l"(bd), "r"(idesc), "r"(0));
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                 :: "r"(smem_u32(&full_bar[mst])) : "memory");
+                    mbar_arrive(smem_u32(&full_bar[mst]));   // releases the row bases of tile u
+                }
+                last_issued = it;
+                // the next tile of this stage: its B slot was last read by the MMA of tile u - 2,
+                // complete since the epilogue drained that tile
+                if (more) {
+                    step(u + 1u);
+                    step(u + 2u);
+                    publish((it + 2u) & (kTcBBufs - 1));
+                }
+                __syncwarp();
             }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            Eb = Eb_n;
-            dR = dR_n;
-            dQ = dQ_n;
-            // ---- segment boundary: merge the buffer into the block list (as in gray_kernel)
-            if ((u & seg_mask) == seg_mask || u < 8u || u + 1 == ntiles) {
-                __syncthreads();
+            it0 += ntiles;
+            continue;
+        }
+
+        // ---------------- epilogue warps
+        refresh();
+        for (unsigned u = 0; u < ntiles; ++u) {
+            const unsigned it = it0 + u, st = it & 1u;
+            if (!aborted) aborted = __any_sync(0xffffffffu, *(volatile int*)&s_abort != 0);
+            float mn = __int_as_float(0x7f800000);      // +inf
+            int base = 0;
+            if (!aborted) {
+                const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&full_bar[st]), (it >> 1) & 1u));
+                if (!ok) {
+                    aborted = true;
+                    if (lane == 0) {
+                        s_abort = 1;
+                        atomicOr(&p.hdr->status, kErrTimeout);
+                    }
+                } else {
+                    base = s.base[(it & (kTcBBufs - 1)) * kTcRows + row];
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    mn = tmem_min128(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + st * (uint32_t)kTcCols +
+                                     (uint32_t)(128 * half));
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                }
+            }
+            // stage st drained: the MMA of tile u + 2 may overwrite it
+            __syncwarp();
+            if (u + 2u < ntiles && lane == 0 && !aborted) mbar_arrive(smem_u32(&ready_bar[st]));
+            // threshold test of this row; exact rescan of its 128 columns when flagged
+            const float thr = (float)(int)((unsigned)tau_scr - (unsigned)base) + delta;
+            if (mn <= thr)
+                tc_rescan(p, s.Jq, s.dQ0 + st * kTcCols, s.Bint, s.E, s.C, &s_buf_count, row, half, (unsigned)base,
+                          u ^ (u >> 1), c0, tau_scr, tie_E, tie_C);
+            // segment boundary: merge the buffer into the block list
+            if ((u & seg_mask) == seg_mask || u < 8u || u + 1u == ntiles) {
+                ep_sync();
                 const unsigned bc = s_buf_count;
-                __syncthreads();
+                ep_sync();
                 if (bc > 0u) {
                     const int lc = s_list_count;
                     const int nb = bc < (unsigned)cap ? (int)bc : cap;
-                    for (int i = tid; i < 2 * cap; i += blockDim.x) {
+                    for (int i = tid; i < 2 * cap; i += kTcEpThreads) {
                         if ((i >= lc && i < cap) || i >= cap + nb) {
                             s.E[i] = kEmptyE;
                             s.C[i] = kEmptyC;
                         }
                     }
-                    block_sort(s.E, s.C, 2 * cap);
+                    group_sort(s.E, s.C, 2 * cap, tid, kTcEpThreads, [] { ep_sync(); });
                     if (tid == 0) {
                         const int total = lc + nb;
                         int keep = total;
@@ -419,19 +526,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant
                         s_list_count = keep;
                         s_buf_count = 0u;
                     }
-                    __syncthreads();
+                    ep_sync();
                 }
                 refresh();
-                if (s_abort) aborted = true;
-            }
-            if (u + 1 < ntiles) {
-                const unsigned u1 = u + 1;
-                cmid ^= 1ull << (kTcSpins + __ffs(u1) - 1);
             }
         }
+        it0 += ntiles;
     }
 
-    // ---- release TMEM (no MMA is in flight: every issued tile was waited for or timed out)
+    // ---- release TMEM once no MMA of this block is in flight
+    if (warp >= kTcEpWarps && lane == 0 && last_issued >= 0 &&
+        !mbar_wait(smem_u32(&full_bar[warp - kTcEpWarps]), ((unsigned)last_issued >> 1) & 1u))
+        atomicOr(&p.hdr->status, kErrTimeout);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -445,9 +551,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant
 
 size_t tc_smem_bytes(int n, int list_cap)
 {
-    return (size_t)kTcRows * 16 * 2 + (size_t)2 * kTcCols * 16 * 2 + (size_t)2 * list_cap * 12 +
+    return (size_t)kTcRows * 16 * 2 + (size_t)kTcBBufs * kTcCols * 16 * 2 + (size_t)2 * list_cap * 12 +
            (size_t)kTcRowBits * kTcCols * 4 + (size_t)kTcMaxWalk * kTcRows * 4 + (size_t)kTcMaxWalk * kTcCols * 4 +
-           (size_t)3 * kTcCols * 4 + (size_t)2 * kTcMaxWalk * 4 + (size_t)kMaxN * 4 + (size_t)n * n * 4;
+           (size_t)2 * kTcCols * 4 + (size_t)kTcBBufs * kTcRows * 4 + (size_t)kTcMaxWalk * kTcMaxWalk * 4 +
+           (size_t)kMaxN * 4 + (size_t)n * n * 4;
 }
 
 cudaError_t launch_tc(const TcParams& p, int grid, cudaStream_t s)
