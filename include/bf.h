@@ -236,6 +236,36 @@ bf_status bf_low_spectrum_backward(const uint64_t* states, const double* grad_E,
                                    bf_dtype out_dtype, void* stream);
 
 /*
+ * Workspace bytes needed by bf_low_spectrum_qubo; 0 for arguments it would
+ * reject.
+ */
+size_t bf_qubo_workspace_size(int n, int S, bf_dtype dtype, const bf_options* opt);
+
+/*
+ * bf_low_spectrum_qubo -- the S lowest (value, configuration) pairs of the
+ * QUBO form of the problem (Sec. 2, Eqs. (2)-(3)) over binary q in {0,1}^n:
+ *
+ *     F(q) = sum_{i<j} a_ij q_i q_j + sum_i b_i q_i
+ *
+ * (the paper's Eq. (2) with the overall sign flipped, as for Eq. (1)).  The
+ * configuration integer is c = sum_i q_i 2^i, the paper's coding of Eq. (4);
+ * ties are broken by ascending c.  The library maps the problem exactly onto
+ * its Ising search: J'_ij = a_ij, h'_i = 2 b_i + sum_{j != i} a_ij (Eq. (3)
+ * scaled by 4) and F = (E' + sum_{i<j} a_ij + 2 sum_i b_i) / 4.
+ *   a          device, n*n values of `dtype`, row-major; strict upper triangle read
+ *   b          device, n values of `dtype`
+ *   F          device out, S values: int64 for BF_I32 (exact), double otherwise
+ *   states     device out, S configuration integers (bit i = q_i)
+ *   workspace  device, >= bf_qubo_workspace_size(...) bytes, 256-byte aligned
+ * Other arguments and options as for bf_low_spectrum (float inputs are
+ * converted to a double Ising instance first).  BF_I32 inputs whose
+ * 2 b_i + sum_j a_ij leaves int32 return BF_EUNSUPPORTED.  The call
+ * synchronises the stream once more than bf_low_spectrum (integer inputs).
+ */
+bf_status bf_low_spectrum_qubo(const void* a, const void* b, int n, int S, bf_dtype dtype, void* F, uint64_t* states,
+                               void* workspace, size_t workspace_bytes, const bf_options* opt, void* stream);
+
+/*
  * Synchronises `stream` and returns the status recorded on the device by the
  * last call that used `workspace` (BF_OK, BF_EOVERFLOW or BF_ETIMEOUT).
  */

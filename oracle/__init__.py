@@ -62,7 +62,12 @@ class Oracle:
         lib.oracle_energy_f64.argtypes = [i32, vp, vp, u64]
         lib.oracle_energy_i64.restype = i64
         lib.oracle_energy_i64.argtypes = [i32, vp, vp, u64]
-        for name in ("oracle_low_spectrum_f64", "oracle_low_spectrum_i64"):
+        lib.oracle_qubo_energy_f64.restype = dbl
+        lib.oracle_qubo_energy_f64.argtypes = [i32, vp, vp, u64]
+        lib.oracle_qubo_energy_i64.restype = i64
+        lib.oracle_qubo_energy_i64.argtypes = [i32, vp, vp, u64]
+        for name in ("oracle_low_spectrum_f64", "oracle_low_spectrum_i64", "oracle_qubo_low_spectrum_f64",
+                     "oracle_qubo_low_spectrum_i64"):
             f = getattr(lib, name)
             f.restype = i32
             f.argtypes = [i32, vp, vp, i32, i32, u64, i32, i32, vp, vp]
@@ -135,6 +140,30 @@ class Oracle:
         if rc != 0:
             raise ValueError(f"oracle_low_spectrum failed rc={rc}")
         return en, states
+
+    # -- QUBO form, Eq. (2) with the library's sign ---------------------------
+    def qubo_energy(self, a, b, c: int):
+        n, a, b = self._prep(a, b)
+        if self._is_int(a):
+            return int(self.lib.oracle_qubo_energy_i64(n, a.ctypes.data, b.ctypes.data, int(c)))
+        return float(self.lib.oracle_qubo_energy_f64(n, a.ctypes.data, b.ctypes.data, int(c)))
+
+    def qubo_low_spectrum(self, a, b, S: int, fixed_bits: int = 0, fixed_value: int = 0,
+                          mode: int = 0, threads: int = 0):
+        """S lowest (F, c) pairs of F(q) = sum_{i<j} a_ij q_i q_j + sum_i b_i q_i, by (F, c)."""
+        n, a, b = self._prep(a, b)
+        states = np.empty(S, dtype=np.uint64)
+        if self._is_int(a):
+            val = np.empty(S, dtype=np.int64)
+            f = self.lib.oracle_qubo_low_spectrum_i64
+        else:
+            val = np.empty(S, dtype=np.float64)
+            f = self.lib.oracle_qubo_low_spectrum_f64
+        rc = f(n, a.ctypes.data, b.ctypes.data, int(S), int(fixed_bits), int(fixed_value),
+               int(mode), int(threads), val.ctypes.data, states.ctypes.data)
+        if rc != 0:
+            raise ValueError(f"oracle_qubo_low_spectrum failed rc={rc}")
+        return val, states
 
     # -- gradient of sum_k g_k E_k (linearity of Eq. (1)) --------------------
     def grad(self, n_list, states, g):

@@ -25,6 +25,10 @@
  *   - Algorithm 1 (Sec. 3): the output is the S lowest configurations sorted
  *     by energy.  The library orders ties by the configuration integer, so
  *     the result is the first S records under the total order (E, c).
+ *   - QUBO form, Sec. 2, Eq. (2), with the same overall sign flip:
+ *         F(q) = + sum_{i<j} a_ij q_i q_j + sum_i b_i q_i ,
+ *     q_i = bit i of c (the binary digits of Eq. (4)); strict upper triangle
+ *     of a read, like J.
  *   - Gradient of L = sum_k g_k E(s^(k)) with respect to J_ij (i<j) and h_i,
  *     which follows from Eq. (1) being linear in J and h:
  *         dL/dJ_ij = sum_k g_k s_i^(k) s_j^(k),   dL/dh_i = sum_k g_k s_i^(k).
@@ -143,6 +147,64 @@ int64_t oracle_energy_i64(int n, const int32_t *J, const int32_t *h, uint64_t c)
 #endif
 }
 
+/* binary variable q_i of configuration c (Sec. 3, Eq. (4)) */
+static int binary_of(uint64_t c, int i)
+{
+    return (int)((c >> i) & 1u);
+}
+
+/* first partner index j of row i in the QUBO pair sum (strict upper triangle) */
+static int qubo_pair_start(int i)
+{
+#if ORACLE_PLANT == 11
+    return i;                          /* planted: diagonal a_ii q_i q_i included */
+#else
+    return i + 1;
+#endif
+}
+
+/* coupling a_ij, i < j, of a row-major matrix */
+static double qubo_coupling_f64(const double *a, int n, int i, int j)
+{
+#if ORACLE_PLANT == 12
+    return a[j * n + i];               /* planted: lower triangle read */
+#else
+    return a[i * n + j];
+#endif
+}
+
+/* Sec. 2, Eq. (2) with the overall sign flipped, FP64 */
+double oracle_qubo_energy_f64(int n, const double *a, const double *b, uint64_t c)
+{
+    double pair = 0.0, field = 0.0;
+    for (int i = 0; i < n; i++) {
+        if (!binary_of(c, i)) continue;
+        for (int j = qubo_pair_start(i); j < n; j++)
+            if (binary_of(c, j)) pair += qubo_coupling_f64(a, n, i, j);
+    }
+    for (int i = 0; i < n; i++)
+        if (binary_of(c, i)) field += b[i];
+    return pair + field;
+}
+
+/* Sec. 2, Eq. (2) for integer coefficients, exact in int64 */
+int64_t oracle_qubo_energy_i64(int n, const int32_t *a, const int32_t *b, uint64_t c)
+{
+    int64_t pair = 0, field = 0;
+    for (int i = 0; i < n; i++) {
+        if (!binary_of(c, i)) continue;
+        for (int j = qubo_pair_start(i); j < n; j++)
+#if ORACLE_PLANT == 12
+            if (binary_of(c, j)) pair += a[j * n + i];
+#else
+            if (binary_of(c, j)) pair += a[i * n + j];
+#endif
+    }
+    for (int i = 0; i < n; i++)
+        if (binary_of(c, i)) field += b[i];
+    return pair + field;
+}
+
 /* ---- selection: first S records under the total order (E, c) ---------- */
 
 typedef struct {
@@ -152,6 +214,7 @@ typedef struct {
 } rec_t;
 
 static int g_is_int; /* set before each selection; read-only while sorting */
+static int g_qubo;   /* 0: Ising energy of Eq. (1), 1: QUBO value of Eq. (2) */
 
 static int rec_less(const rec_t *a, const rec_t *b)
 {
@@ -207,10 +270,12 @@ static rec_t make_rec(int n, const void *J, const void *h, uint64_t c)
     rec_t r;
     r.c = c;
     if (g_is_int) {
-        r.ie = oracle_energy_i64(n, (const int32_t *)J, (const int32_t *)h, c);
+        r.ie = g_qubo ? oracle_qubo_energy_i64(n, (const int32_t *)J, (const int32_t *)h, c)
+                      : oracle_energy_i64(n, (const int32_t *)J, (const int32_t *)h, c);
         r.e = (double)r.ie;
     } else {
-        r.e = oracle_energy_f64(n, (const double *)J, (const double *)h, c);
+        r.e = g_qubo ? oracle_qubo_energy_f64(n, (const double *)J, (const double *)h, c)
+                     : oracle_energy_f64(n, (const double *)J, (const double *)h, c);
         r.ie = 0;
     }
     return r;
@@ -225,10 +290,11 @@ static rec_t make_rec(int n, const void *J, const void *h, uint64_t c)
  * 2 = per-thread bounded heaps.  threads <= 0 uses the OpenMP default.
  * Returns 0 on success, -1 on invalid arguments, -2 when memory is short.
  */
-static int low_spectrum(int is_int, int n, const void *J, const void *h, int S,
+static int low_spectrum(int is_int, int qubo, int n, const void *J, const void *h, int S,
                         int fixed_bits, uint64_t fixed_value, int mode, int threads,
                         rec_t *out)
 {
+    g_qubo = qubo;
     if (n < 1 || n > 64 || S < 1 || fixed_bits < 0 || fixed_bits > n) return -1;
     int free_bits = n - fixed_bits;
     if (free_bits > 62) return -1;
@@ -308,7 +374,7 @@ int oracle_low_spectrum_f64(int n, const double *J, const double *h, int S,
     if (S < 1) return -1;
     rec_t *out = (rec_t *)malloc(sizeof(rec_t) * (size_t)S);
     if (!out) return -2;
-    int rc = low_spectrum(0, n, J, h, S, fixed_bits, fixed_value, mode, threads, out);
+    int rc = low_spectrum(0, 0, n, J, h, S, fixed_bits, fixed_value, mode, threads, out);
     if (rc == 0)
         for (int k = 0; k < S; k++) { out_e[k] = out[k].e; out_c[k] = out[k].c; }
     free(out);
@@ -322,9 +388,39 @@ int oracle_low_spectrum_i64(int n, const int32_t *J, const int32_t *h, int S,
     if (S < 1) return -1;
     rec_t *out = (rec_t *)malloc(sizeof(rec_t) * (size_t)S);
     if (!out) return -2;
-    int rc = low_spectrum(1, n, J, h, S, fixed_bits, fixed_value, mode, threads, out);
+    int rc = low_spectrum(1, 0, n, J, h, S, fixed_bits, fixed_value, mode, threads, out);
     if (rc == 0)
         for (int k = 0; k < S; k++) { out_e[k] = out[k].ie; out_c[k] = out[k].c; }
+    free(out);
+    return rc;
+}
+
+/* The S lowest (F, c) of the QUBO form (Sec. 2, Eq. (2)), FP64 */
+int oracle_qubo_low_spectrum_f64(int n, const double *a, const double *b, int S,
+                                 int fixed_bits, uint64_t fixed_value, int mode, int threads,
+                                 double *out_f, uint64_t *out_c)
+{
+    if (S < 1) return -1;
+    rec_t *out = (rec_t *)malloc(sizeof(rec_t) * (size_t)S);
+    if (!out) return -2;
+    int rc = low_spectrum(0, 1, n, a, b, S, fixed_bits, fixed_value, mode, threads, out);
+    if (rc == 0)
+        for (int k = 0; k < S; k++) { out_f[k] = out[k].e; out_c[k] = out[k].c; }
+    free(out);
+    return rc;
+}
+
+/* The S lowest (F, c) of the QUBO form for integer coefficients, exact */
+int oracle_qubo_low_spectrum_i64(int n, const int32_t *a, const int32_t *b, int S,
+                                 int fixed_bits, uint64_t fixed_value, int mode, int threads,
+                                 int64_t *out_f, uint64_t *out_c)
+{
+    if (S < 1) return -1;
+    rec_t *out = (rec_t *)malloc(sizeof(rec_t) * (size_t)S);
+    if (!out) return -2;
+    int rc = low_spectrum(1, 1, n, a, b, S, fixed_bits, fixed_value, mode, threads, out);
+    if (rc == 0)
+        for (int k = 0; k < S; k++) { out_f[k] = out[k].ie; out_c[k] = out[k].c; }
     free(out);
     return rc;
 }

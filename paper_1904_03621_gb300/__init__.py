@@ -6,10 +6,10 @@ first use and raise if it is missing.
 """
 import importlib
 
-__all__ = ["instances", "low_spectrum", "low_spectrum_batched", "low_spectrum_backward",
-           "LowSpectrumFn", "lib"]
+__all__ = ["instances", "low_spectrum", "low_spectrum_batched", "low_spectrum_backward", "low_spectrum_qubo",
+           "LowSpectrumFn", "search", "Solution", "lib"]
 
-_API = ("low_spectrum", "low_spectrum_batched", "low_spectrum_backward", "LowSpectrumFn")
+_API = ("low_spectrum", "low_spectrum_batched", "low_spectrum_backward", "low_spectrum_qubo", "LowSpectrumFn")
 
 
 def __getattr__(name):
@@ -17,6 +17,8 @@ def __getattr__(name):
         return importlib.import_module(__name__ + ".instances")
     if name == "lib":
         return importlib.import_module(__name__ + "._lib")
+    if name in ("search", "Solution", "graph_to_dense"):
+        return getattr(importlib.import_module(__name__ + ".graph"), name)
     if name in _API:
         return getattr(importlib.import_module(__name__ + ".api"), name)
     raise AttributeError(name)

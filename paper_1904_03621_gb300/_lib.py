@@ -12,11 +12,12 @@ LIB_PATH = os.path.join(_PKG, "libbf.so")
 
 BF_OK, BF_EINVAL, BF_ECUDA, BF_EOVERFLOW, BF_ETIMEOUT, BF_EUNSUPPORTED, BF_EWORKSPACE = range(7)
 BF_I32, BF_F32, BF_F64 = 0, 1, 2
-BF_VARIANT_AUTO, BF_VARIANT_GRAY = 0, 1
+BF_VARIANT_AUTO, BF_VARIANT_GRAY, BF_VARIANT_TC = 0, 1, 2
 
 # every symbol include/bf.h declares
 EXPORTS = ["bf_workspace_size", "bf_low_spectrum", "bf_low_spectrum_noalloc", "bf_batched_workspace_size",
-           "bf_low_spectrum_batched", "bf_autotune_batched", "bf_low_spectrum_backward", "bf_workspace_status",
+           "bf_low_spectrum_batched", "bf_autotune_batched", "bf_low_spectrum_backward", "bf_qubo_workspace_size",
+           "bf_low_spectrum_qubo", "bf_workspace_status",
            "bf_last_profile", "bf_launch_count", "bf_merge_lists", "bf_status_string", "bf_last_error_detail",
            "bf_version"]
 
@@ -64,6 +65,10 @@ def load(path: str | None = None):
                                         ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_float)]
     lib.bf_low_spectrum_backward.restype = i32
     lib.bf_low_spectrum_backward.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, vp, i32, vp]
+    lib.bf_qubo_workspace_size.restype = sz
+    lib.bf_qubo_workspace_size.argtypes = [i32, i32, i32, ctypes.POINTER(Options)]
+    lib.bf_low_spectrum_qubo.restype = i32
+    lib.bf_low_spectrum_qubo.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, sz, ctypes.POINTER(Options), vp]
     lib.bf_merge_lists.restype = i32
     lib.bf_merge_lists.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(vp), i32, i32, i32, vp, vp]
     lib.bf_workspace_status.restype = i32

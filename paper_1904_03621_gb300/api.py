@@ -78,6 +78,44 @@ def low_spectrum(J: torch.Tensor, h: torch.Tensor, S: int, *, variant: int = 0, 
     return energies, states
 
 
+def low_spectrum_qubo(a: torch.Tensor, b: torch.Tensor, S: int, *, variant: int = 0, fixed_bits: int = 0,
+                      fixed_value: int = 0, task_log2: int = 0, grid_blocks: int = 0, spill_log2: int = 0,
+                      stream=None, workspace: torch.Tensor | None = None, check: bool = True):
+    """S lowest (F, configuration) pairs of the QUBO form (Sec. 2, Eqs. (2)-(3)).
+
+    F(q) = sum_{i<j} a_ij q_i q_j + sum_i b_i q_i over q in {0,1}^n (the paper's Eq. (2)
+    with the overall sign flipped, as for Eq. (1)); configuration bit i = q_i.
+    a: (n, n) CUDA tensor (int32, float32 or float64), strict upper triangle read; b: (n,).
+    Returns (F, states): F int64 (exact, int32 input) or float64.
+    """
+    lib = _lib.load()
+    if a.dtype not in _DTYPES or b.dtype != a.dtype:
+        raise TypeError("a and b must share one of int32, float32, float64")
+    if not (a.is_cuda and b.is_cuda):
+        raise ValueError("a and b must be CUDA tensors")
+    n = a.shape[0]
+    a = a.contiguous()
+    b = b.contiguous()
+    o = _options(variant, fixed_bits, fixed_value, task_log2, grid_blocks, spill_log2, 0)
+    nbytes = lib.bf_qubo_workspace_size(n, S, _DTYPES[a.dtype], ctypes.byref(o))
+    if nbytes == 0:
+        _lib.check(lib.bf_low_spectrum_qubo(None, None, n, S, _DTYPES[a.dtype], None, None, None, 0,
+                                            ctypes.byref(o), None), lib)
+        raise _lib.BFError(_lib.BF_EINVAL, lib.bf_last_error_detail().decode())
+    if workspace is None or workspace.numel() < nbytes:
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device=a.device)
+    edt = torch.int64 if a.dtype == torch.int32 else torch.float64
+    F = torch.empty(S, dtype=edt, device=a.device)
+    states = torch.empty(S, dtype=torch.int64, device=a.device)
+    sh = _stream_handle(stream)
+    st = lib.bf_low_spectrum_qubo(a.data_ptr(), b.data_ptr(), n, S, _DTYPES[a.dtype], F.data_ptr(),
+                                  states.data_ptr(), workspace.data_ptr(), workspace.numel(), ctypes.byref(o), sh)
+    _lib.check(st, lib)
+    if check:
+        _lib.check(lib.bf_workspace_status(workspace.data_ptr(), sh), lib)
+    return F, states
+
+
 def states_u64(states: torch.Tensor) -> np.ndarray:
     """Configuration integers as numpy uint64 (the int64 tensor holds their bits)."""
     return states.detach().cpu().numpy().view(np.uint64)

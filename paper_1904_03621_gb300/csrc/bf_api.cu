@@ -158,6 +158,33 @@ cudaError_t merge_tree(int* AE, unsigned long long* AC, int* BE, unsigned long l
 
 }  // namespace
 
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// the converted Ising instance lives after the inner search's workspace
+struct QuboLayout {
+    size_t inner, J, h, off, flag, total;
+};
+
+bf_status qubo_layout(int n, int S, bf_dtype dtype, const bf_options* opt, QuboLayout& q)
+{
+    const bf_dtype inner_dt = dtype == BF_I32 ? BF_I32 : BF_F64;
+    Plan pl;
+    bf_status st = make_plan(n, S, inner_dt, opt, pl);
+    if (st != BF_OK) return st;
+    const size_t elt = dtype == BF_I32 ? 4 : 8;
+    q.inner = align256(pl.bytes);
+    q.J = q.inner;
+    q.h = q.J + align256((size_t)n * n * elt);
+    q.off = q.h + align256((size_t)n * elt);
+    q.flag = q.off + 8;
+    q.total = q.off + 256;
+    return BF_OK;
+}
+
+}  // namespace
+
 namespace bf {
 bf_status report(bf_status s, const char* detail) { return fail(s, "%s", detail); }
 }  // namespace bf
@@ -322,6 +349,50 @@ bf_status bf_workspace_status(const void* workspace, void* stream_ptr)
     if (status & bf::kErrTimeout) return fail(BF_ETIMEOUT, "bounded device wait expired (device status 0x%x)", status);
     if (status & bf::kErrRange) return fail(BF_EUNSUPPORTED, "instance outside the fixed-point range (0x%x)", status);
     if (status & bf::kErrArg) return fail(BF_EINVAL, "an instance's n is outside the supported range (0x%x)", status);
+    return BF_OK;
+}
+
+// ---- QUBO form (Sec. 2, Eqs. (2)-(3)) -----------------------------------
+
+size_t bf_qubo_workspace_size(int n, int S, bf_dtype dtype, const bf_options* opt)
+{
+    QuboLayout q;
+    if (qubo_layout(n, S, dtype, opt, q) != BF_OK) return 0;
+    return q.total;
+}
+
+bf_status bf_low_spectrum_qubo(const void* a, const void* b, int n, int S, bf_dtype dtype, void* F, uint64_t* states,
+                               void* workspace, size_t workspace_bytes, const bf_options* opt, void* stream_ptr)
+{
+    g_detail.clear();
+    if (dtype != BF_I32 && dtype != BF_F32 && dtype != BF_F64) return fail(BF_EINVAL, "unknown dtype %d", dtype);
+    QuboLayout q;
+    bf_status st = qubo_layout(n, S, dtype, opt, q);
+    if (st != BF_OK) return st;
+    if (!a || !b || !F || !states || !workspace) return fail(BF_EINVAL, "null pointer argument");
+    if (workspace_bytes < q.total)
+        return fail(BF_EWORKSPACE, "workspace of %zu bytes < %zu required", workspace_bytes, q.total);
+    if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return fail(BF_EWORKSPACE, "workspace not 256-byte aligned");
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    char* ws = static_cast<char*>(workspace);
+    auto* flag = reinterpret_cast<unsigned*>(ws + q.flag);
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(unsigned), stream);
+    if (e == cudaSuccess)
+        e = bf::launch_qubo_prep(a, b, n, (int)dtype, ws + q.J, ws + q.h, ws + q.off, flag, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "QUBO map");
+    if (dtype == BF_I32) {
+        unsigned hflag = 0;
+        e = cudaMemcpyAsync(&hflag, flag, sizeof(hflag), cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) return cuda_fail(e, "QUBO map status");
+        if (hflag) return fail(BF_EUNSUPPORTED, "2 b_i + sum_j a_ij outside int32: use a float dtype");
+    }
+    const bf_dtype inner_dt = dtype == BF_I32 ? BF_I32 : BF_F64;
+    st = bf_low_spectrum(ws + q.J, ws + q.h, n, S, inner_dt, F, states, workspace, q.inner, opt, stream_ptr);
+    if (st != BF_OK) return st;
+    auto* hdr = reinterpret_cast<bf::WsHeader*>(ws);
+    e = bf::launch_qubo_finish(F, S, dtype == BF_I32 ? 0 : 1, ws + q.off, &hdr->status, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "QUBO offset");
     return BF_OK;
 }
 

@@ -250,6 +250,11 @@ cudaError_t launch_seed(const Prep* prep, int n, int free_bits, unsigned long lo
 // hdr->tau = E[S - 1] of a merged list; resets the task and spill counters.
 cudaError_t launch_set_tau(const int* E, int S, WsHeader* hdr, cudaStream_t s);
 // Small instances (<= 2^kSmallFreeBits configurations): direct enumeration.
+// QUBO mapping (k_qubo.cu): dtype 0 = int32 in / int32 out (int64 offset), 1 = float in, 2 = double in
+// (double out and offset for both)
+cudaError_t launch_qubo_prep(const void* a, const void* b, int n, int dtype, void* Jout, void* hout, void* off4,
+                             unsigned* flag, cudaStream_t s);
+cudaError_t launch_qubo_finish(void* F, int S, int dtype, const void* off4, unsigned* flag, cudaStream_t s);
 cudaError_t launch_direct(const void* J, const void* h, int n, int dtype, int S, int free_bits,
                           unsigned long long hiconst, void* energies, unsigned long long* states,
                           WsHeader* hdr, cudaStream_t s);

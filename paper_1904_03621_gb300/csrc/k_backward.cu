@@ -13,7 +13,6 @@ namespace bf {
 namespace {
 
 constexpr int kBackThreads = 256;
-constexpr int kBackMaxS = 4096;
 
 __global__ void __launch_bounds__(kBackThreads) backward_kernel(const unsigned long long* states, const double* g,
                                                                 const int* n_arr, int S, const long long* J_off,

@@ -307,8 +307,70 @@ def pin_grad(o):
             assert abs(fd - dh[h_off[b] + i]) < 1e-8, f"dh[{i}]"
 
 
+def _qubo_instance(rng, n, integer):
+    """Random QUBO coefficients with junk on the diagonal and lower triangle of a
+    (which Eq. (2)'s pair sum over i < j must ignore)."""
+    if integer:
+        a = rng.integers(-9, 10, (n, n)).astype(np.int32)
+        b = rng.integers(-9, 10, n).astype(np.int32)
+    else:
+        a = rng.standard_normal((n, n))
+        b = rng.standard_normal(n)
+    return a, b
+
+
+def pin_qubo_closed_forms(o):
+    """Sec. 2, Eq. (2) (library sign) at configurations where the sum collapses:
+    F(0) = 0, F(e_i) = b_i, F(e_i + e_j) = a_ij + b_i + b_j (i < j)."""
+    rng = np.random.default_rng(21)
+    for integer in (True, False):
+        n = 9
+        a, b = _qubo_instance(rng, n, integer)
+        assert o.qubo_energy(a, b, 0) == 0
+        for i in range(n):
+            assert o.qubo_energy(a, b, 1 << i) == b[i]
+            for j in range(i + 1, n):
+                want = a[i, j] + b[i] + b[j]
+                got = o.qubo_energy(a, b, (1 << i) | (1 << j))
+                assert (got == want) if integer else abs(got - want) < 1e-12, (i, j)
+
+
+def pin_qubo_ising_map(o):
+    """Sec. 2, Eq. (3): with J_ij = a_ij / 4 (i < j) and h_i = b_i / 2 + sum_{j != i} a_ij / 4
+    (library sign), E(s) - F(q) = sum_{i<j} J_ij - sum_i h_i for every configuration; the
+    low spectra agree configuration by configuration (the offset is a constant)."""
+    rng = np.random.default_rng(22)
+    n = 10
+    a, b = _qubo_instance(rng, n, integer=False)
+    U = np.triu(a, 1)
+    J = U / 4.0
+    h = b / 2.0 + (U + U.T).sum(axis=1) / 4.0
+    offset = np.triu(J, 1).sum() - h.sum()
+    e = o.all_energies(J, h)
+    for c in range(1 << n):
+        assert abs(e[c] - o.qubo_energy(a, b, c) - offset) < 1e-10, c
+    f_q, c_q = o.qubo_low_spectrum(a, b, 40)
+    e_i, c_i = o.low_spectrum(J, h, 40)
+    assert np.array_equal(c_q, c_i)
+    assert np.abs((e_i - offset) - f_q).max() < 1e-10
+
+
+def pin_qubo_separable(o):
+    """a = 0: F(q) = sum_i b_i q_i, minimised by q_i = [b_i < 0] with value sum of the
+    negative b_i; the next state flips the b_i of smallest magnitude."""
+    rng = np.random.default_rng(23)
+    n = 12
+    b = rng.standard_normal(n)
+    a = np.zeros((n, n))
+    f, c = o.qubo_low_spectrum(a, b, 2)
+    mask = sum(1 << i for i in range(n) if b[i] < 0)
+    assert c[0] == mask and abs(f[0] - b[b < 0].sum()) < 1e-12
+    k = int(np.argmin(np.abs(b)))
+    assert c[1] == mask ^ (1 << k) and abs(f[1] - (f[0] + abs(b[k]))) < 1e-12
+
+
 ALL_PINS = [
     pin_paper_example, pin_coding_example, pin_ferromagnet, pin_fields_only, pin_z2, pin_gauge,
     pin_qubo, pin_sum_zero, pin_matrix_form, pin_full_sort, pin_ties, pin_streaming_equals_sort,
-    pin_subspace, pin_grad,
+    pin_subspace, pin_grad, pin_qubo_closed_forms, pin_qubo_ising_map, pin_qubo_separable,
 ]

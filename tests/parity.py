@@ -26,8 +26,12 @@ def assert_int_equal(en_gpu, st_gpu, en_or, st_or):
         f"states differ at ranks {np.nonzero(np.asarray(st_gpu, np.uint64) != np.asarray(st_or, np.uint64))[0][:10]}"
 
 
-def assert_float_parity(o, J, h, en_gpu, st_gpu, en_or_s1, st_or_s1):
-    """en_or_s1 / st_or_s1: oracle result with S + 1 records (or S when S = 2^n)."""
+def assert_float_parity(o, J, h, en_gpu, st_gpu, en_or_s1, st_or_s1, energy=None):
+    """en_or_s1 / st_or_s1: oracle result with S + 1 records (or S when S = 2^n).
+
+    energy(J, h, c): the oracle's value of one configuration (default: Eq. (1),
+    o.energy; pass o.qubo_energy for the QUBO form, J = a, h = b)."""
+    energy = energy or o.energy
     S = len(en_gpu)
     tol = tolerance(J, h)
     en_gpu = np.asarray(en_gpu, dtype=np.float64)
@@ -38,7 +42,7 @@ def assert_float_parity(o, J, h, en_gpu, st_gpu, en_or_s1, st_or_s1):
     assert err.max() <= tol, f"max energy error {err.max():.3e} > tol {tol:.3e} at rank {err.argmax()}"
     assert len(set(st_gpu.tolist())) == S, "duplicate states"
     for k in range(S):
-        e = o.energy(J, h, int(st_gpu[k]))
+        e = energy(J, h, int(st_gpu[k]))
         assert abs(e - en_gpu[k]) <= tol, f"rank {k}: state {st_gpu[k]} has E={e}, returned {en_gpu[k]}"
     assert np.all(np.diff(en_gpu) >= -tol), "energies not ascending"
     if len(en_or_s1) > S:

@@ -42,3 +42,17 @@ def test_host_only_calls_without_gpu():
     assert st == _lib.BF_EINVAL
     assert lib.bf_last_error_detail() != b""
     assert lib.bf_launch_count() >= 0
+
+
+def test_graph_to_dense_marshalling():
+    """Dict graph -> dense (J, h): fields from (i, i), pairs accumulated into the upper
+    triangle in sorted-label order, dtype int32 for integer weights."""
+    import numpy as np
+    from paper_1904_03621_gb300.graph import graph_to_dense
+    J, h, nodes = graph_to_dense({("b", "a"): 2, ("a", "b"): 3, ("c", "c"): -1, ("a", "a"): 4})
+    assert nodes == ["a", "b", "c"]
+    assert J.dtype == np.int32 and h.dtype == np.int32
+    assert J.tolist() == [[0, 5, 0], [0, 0, 0], [0, 0, 0]]
+    assert h.tolist() == [4, 0, -1]
+    J, h, _ = graph_to_dense({(1, 2): 0.5})
+    assert J.dtype == np.float64 and J[0, 1] == 0.5

@@ -3,7 +3,8 @@
 This shows the pins are sensitive to the plausible errors they guard
 against: a dropped field term, a flipped sign, the wrong triangle of J, the
 diagonal included, reversed or inverted bit encoding, reversed tie order, a
-lost record, a wrong gradient factor and single-precision accumulation.
+lost record, a wrong gradient factor, single-precision accumulation and, for the
+QUBO form, the diagonal or the lower triangle of a read.
 """
 import pytest
 
@@ -21,6 +22,8 @@ PLANTS = {
     8: "first record lost in selection",
     9: "gradient uses s_i instead of s_i s_j",
     10: "energy accumulated in single precision",
+    11: "QUBO pair sum includes the diagonal",
+    12: "QUBO pairs read from the lower triangle",
 }
 
 
