@@ -241,6 +241,56 @@ def batched_section(api, torch, dev, steps, warmup):
     return out
 
 
+FIG3_K = {16: 100, 18: 100, 20: 100, 22: 100, 24: 100, 26: 100, 28: 100, 30: 100, 32: 100, 34: 100, 36: 100,
+          38: 50, 40: 20, 42: 5, 44: 2, 46: 1, 48: 1, 50: 1}
+
+
+def fig3_sweep(args):
+    """Time to solution against N (the paper's Fig. 3, Sec. 5.1): fully connected instances,
+    J_ij ~ N(0,1), h_i ~ N(0,1), S = 100, K instances per N (seeds 0..K-1).  Each search is
+    one public-API call on inputs resident in HBM, timed with CUDA events; one JSON line per
+    N, then estimates for N > 50 from the per-configuration time of the N = 48 search (the
+    paper estimates large N from the time of one chunk the same way)."""
+    import torch
+    from paper_1904_03621_gb300 import build, instances
+    build.build()
+    from paper_1904_03621_gb300 import api
+    dev = torch.device("cuda", 0)
+    S = 100
+    stream = torch.cuda.current_stream()
+    Jw, hw = instances.dense_gaussian(30, 999)
+    api.low_spectrum(torch.tensor(Jw, device=dev), torch.tensor(hw, device=dev), S)   # warm-up
+    rows = []
+    n_max = args.fig3_max_n
+    for n in sorted(k for k in FIG3_K if k <= n_max):
+        times = []
+        for seed in range(FIG3_K[n]):
+            J, h = instances.dense_gaussian(n, seed)
+            Jd, hd = torch.tensor(J, device=dev), torch.tensor(h, device=dev)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            api.low_spectrum(Jd, hd, S, check=False)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            times.append(ev0.elapsed_time(ev1) / 1e3)
+        t = np.asarray(times)
+        row = {"fig3": True, "N": n, "S": S, "instances": len(times), "median_s": float(np.median(t)),
+               "mean_s": float(t.mean()), "min_s": float(t.min()), "max_s": float(t.max()),
+               "configs_per_s": float(2.0 ** n / np.median(t)), "measured": True}
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    ref = [r for r in rows if r["N"] == 48]
+    if ref:
+        per_config = ref[0]["median_s"] / 2.0 ** 48
+        for n in (52, 54, 56, 58, 60, 62, 64):
+            row = {"fig3": True, "N": n, "S": S, "estimate_s": per_config * 2.0 ** n,
+                   "estimate_days": per_config * 2.0 ** n / 86400.0, "measured": False}
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -252,7 +302,12 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--variant", default="gray", choices=["gray", "tc"],
                     help="screening kernel: Gray-code walk or tensor-core tiles")
+    ap.add_argument("--fig3", action="store_true",
+                    help="time-to-solution sweep over N (the paper's Fig. 3) instead of the benchmark line")
+    ap.add_argument("--fig3-max-n", type=int, default=50)
     args = ap.parse_args()
+    if args.fig3:
+        return fig3_sweep(args)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

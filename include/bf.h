@@ -266,6 +266,55 @@ bf_status bf_low_spectrum_qubo(const void* a, const void* b, int n, int S, bf_dt
                                void* workspace, size_t workspace_bytes, const bf_options* opt, void* stream);
 
 /*
+ * Resumable search (checkpoint / restart).  Algorithm 1 (Sec. 3) processes the
+ * configuration space in chunks, c = offset + index (Eq. (6)), keeping the S
+ * lowest records seen so far.  A cursor holds that state between chunks: the
+ * 2^chunk_bits chunks are the subspaces whose top chunk_bits configuration
+ * bits equal the chunk number, and the cursor records the next chunk and the
+ * running list.  It is a caller-owned host buffer of bf_cursor_bytes(S)
+ * bytes, self-describing and position independent (128-byte header with a
+ * checksum, then S energies and S states), so it can be written to a file
+ * and passed back after a restart.  The final list equals bf_low_spectrum's
+ * result for the whole space (every candidate's energy is evaluated per
+ * configuration, so chunking changes nothing).
+ */
+
+/* FNV-1a 64 digest of an instance (n, dtype, strict upper triangle of J, h); host memory. */
+uint64_t bf_instance_digest(const void* J_host, const void* h_host, int n, bf_dtype dtype);
+
+/* Bytes of a cursor for S states (0 if S is outside [1, BF_MAX_S]). */
+size_t bf_cursor_bytes(int S);
+
+/*
+ * Initialises a cursor for an n-spin instance of `dtype` whose digest is
+ * `digest` (bf_instance_digest), split into 2^chunk_bits chunks
+ * (0 <= chunk_bits <= min(n, 40), S <= 2^(n - chunk_bits)).  Host only.
+ */
+bf_status bf_cursor_init(void* cursor, size_t cursor_bytes, int n, int S, bf_dtype dtype, int chunk_bits,
+                         uint64_t digest);
+
+/* Workspace bytes bf_cursor_step needs with these options (0 if rejected; fixed_bits must be 0). */
+size_t bf_cursor_workspace_size(const void* cursor, size_t cursor_bytes, const bf_options* opt);
+
+/*
+ * Searches up to max_chunks further chunks on the GPU and merges each chunk's S
+ * records into the cursor (host), which is consistent (checksum resealed)
+ * after every chunk.  J, h: device, the instance the cursor was made for (its
+ * digest is checked, after a device-to-host copy).  Synchronises the stream
+ * after every chunk.  Device-side conditions are returned directly.
+ */
+bf_status bf_cursor_step(void* cursor, size_t cursor_bytes, const void* J, const void* h, int max_chunks,
+                         void* workspace, size_t workspace_bytes, const bf_options* opt, void* stream);
+
+/*
+ * Reads a cursor (host): next chunk, number of chunks, and the current list
+ * (count records, ascending by (E, c); int64 energies for BF_I32, double
+ * otherwise).  Any output pointer may be NULL.
+ */
+bf_status bf_cursor_state(const void* cursor, size_t cursor_bytes, uint64_t* next_chunk, uint64_t* total_chunks,
+                          void* energies_host, uint64_t* states_host, int* count);
+
+/*
  * Synchronises `stream` and returns the status recorded on the device by the
  * last call that used `workspace` (BF_OK, BF_EOVERFLOW or BF_ETIMEOUT).
  */
