@@ -266,6 +266,33 @@ bf_status bf_low_spectrum_qubo(const void* a, const void* b, int n, int S, bf_dt
                                void* workspace, size_t workspace_bytes, const bf_options* opt, void* stream);
 
 /*
+ * q-state Potts model -- one of the other classical spin-glass models to
+ * which Sec. 2 says the method extends (its Ref. Wu82).  Energy, with the
+ * same sign convention as Eq. (1) here:
+ *
+ *     E(sigma) = sum_{i<j} J_ij [sigma_i == sigma_j] + sum_i h_i(sigma_i),
+ *
+ * sigma_i in {0, ..., q-1}, 2 <= q <= 8, configuration integer
+ * c = sum_i sigma_i q^i (base-q digits; the binary coding of Sec. 3, Eq. (4)
+ * for q = 2).  q^n <= 2^62.  Ties are broken by ascending c.  For q = 2 the
+ * model is an Ising instance with couplings J/2.
+ *   J          device, n*n values of `dtype`, row-major; strict upper triangle read
+ *   h          device, n*q values of `dtype`, row-major: h[i*q + v] = h_i(v)
+ *   energies   device out, S values: int64 for BF_I32 (exact), double otherwise
+ *              (FP64 re-evaluation of every candidate, as for bf_low_spectrum)
+ *   states     device out, S configuration integers
+ *   workspace  device, >= bf_potts_workspace_size(...) bytes, 256-byte aligned
+ * Options: task/grid/spill/profile fields as for bf_low_spectrum; fixed_bits
+ * and the tensor-core variant are not supported (BF_EINVAL).  The call
+ * synchronises once after its preparation kernel.
+ */
+size_t bf_potts_workspace_size(int n, int q, int S, bf_dtype dtype, const bf_options* opt);
+
+bf_status bf_low_spectrum_potts(const void* J, const void* h, int n, int q, int S, bf_dtype dtype, void* energies,
+                                uint64_t* states, void* workspace, size_t workspace_bytes, const bf_options* opt,
+                                void* stream);
+
+/*
  * Resumable search (checkpoint / restart).  Algorithm 1 (Sec. 3) processes the
  * configuration space in chunks, c = offset + index (Eq. (6)), keeping the S
  * lowest records seen so far.  A cursor holds that state between chunks: the

@@ -62,6 +62,14 @@ class Oracle:
         lib.oracle_energy_f64.argtypes = [i32, vp, vp, u64]
         lib.oracle_energy_i64.restype = i64
         lib.oracle_energy_i64.argtypes = [i32, vp, vp, u64]
+        lib.oracle_potts_energy_f64.restype = dbl
+        lib.oracle_potts_energy_f64.argtypes = [i32, i32, vp, vp, u64]
+        lib.oracle_potts_energy_i64.restype = i64
+        lib.oracle_potts_energy_i64.argtypes = [i32, i32, vp, vp, u64]
+        for name in ("oracle_potts_low_spectrum_f64", "oracle_potts_low_spectrum_i64"):
+            f = getattr(lib, name)
+            f.restype = i32
+            f.argtypes = [i32, i32, vp, vp, i32, i32, i32, vp, vp]
         lib.oracle_qubo_energy_f64.restype = dbl
         lib.oracle_qubo_energy_f64.argtypes = [i32, vp, vp, u64]
         lib.oracle_qubo_energy_i64.restype = i64
@@ -164,6 +172,39 @@ class Oracle:
         if rc != 0:
             raise ValueError(f"oracle_qubo_low_spectrum failed rc={rc}")
         return val, states
+
+    # -- q-state Potts model ------------------------------------------------------
+    @staticmethod
+    def _prep_potts(J, h):
+        J = np.asarray(J)
+        h = np.asarray(h)
+        n, q = h.shape
+        assert J.shape == (n, n)
+        dt = np.int32 if np.issubdtype(J.dtype, np.integer) else np.float64
+        return n, q, np.ascontiguousarray(J, dtype=dt), np.ascontiguousarray(h, dtype=dt)
+
+    def potts_energy(self, J, h, c: int):
+        """E = sum_{i<j} J_ij [sigma_i == sigma_j] + sum_i h[i, sigma_i], sigma_i = base-q digit i of c."""
+        n, q, J, h = self._prep_potts(J, h)
+        if self._is_int(J):
+            return int(self.lib.oracle_potts_energy_i64(n, q, J.ctypes.data, h.ctypes.data, int(c)))
+        return float(self.lib.oracle_potts_energy_f64(n, q, J.ctypes.data, h.ctypes.data, int(c)))
+
+    def potts_low_spectrum(self, J, h, S: int, mode: int = 0, threads: int = 0):
+        """S lowest (E, c) of the Potts model (h of shape (n, q)), ordered by (E, c)."""
+        n, q, J, h = self._prep_potts(J, h)
+        states = np.empty(S, dtype=np.uint64)
+        if self._is_int(J):
+            en = np.empty(S, dtype=np.int64)
+            f = self.lib.oracle_potts_low_spectrum_i64
+        else:
+            en = np.empty(S, dtype=np.float64)
+            f = self.lib.oracle_potts_low_spectrum_f64
+        rc = f(n, q, J.ctypes.data, h.ctypes.data, int(S), int(mode), int(threads), en.ctypes.data,
+               states.ctypes.data)
+        if rc != 0:
+            raise ValueError(f"oracle_potts_low_spectrum failed rc={rc}")
+        return en, states
 
     # -- gradient of sum_k g_k E_k (linearity of Eq. (1)) --------------------
     def grad(self, n_list, states, g):

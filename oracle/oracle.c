@@ -29,6 +29,10 @@
  *         F(q) = + sum_{i<j} a_ij q_i q_j + sum_i b_i q_i ,
  *     q_i = bit i of c (the binary digits of Eq. (4)); strict upper triangle
  *     of a read, like J.
+ *   - q-state Potts model (Sec. 2: the extension to other classical
+ *     spin-glass models), same sign convention:
+ *         E(sigma) = sum_{i<j} J_ij [sigma_i == sigma_j] + sum_i h_i(sigma_i),
+ *     sigma_i = base-q digit i of c, h stored as h[i*q + v].
  *   - Gradient of L = sum_k g_k E(s^(k)) with respect to J_ij (i<j) and h_i,
  *     which follows from Eq. (1) being linear in J and h:
  *         dL/dJ_ij = sum_k g_k s_i^(k) s_j^(k),   dL/dh_i = sum_k g_k s_i^(k).
@@ -205,6 +209,65 @@ int64_t oracle_qubo_energy_i64(int n, const int32_t *a, const int32_t *b, uint64
     return pair + field;
 }
 
+/* base-q digit i of configuration c (generalising Sec. 3, Eq. (4)) */
+static int digit_of(uint64_t c, int i, int q)
+{
+    for (int k = 0; k < i; k++) c /= (uint64_t)q;
+    return (int)(c % (uint64_t)q);
+}
+
+/* the indicator [sigma_i == sigma_j] of the Potts pair term */
+static int same_state(int a, int b)
+{
+#if ORACLE_PLANT == 13
+    return a != b;                     /* planted: inequality */
+#else
+    return a == b;
+#endif
+}
+
+/* field h_i(v) of a row-major n x q table */
+static double potts_field_f64(const double *h, int n, int q, int i, int v)
+{
+#if ORACLE_PLANT == 14
+    (void)q;
+    return h[v * n + i];               /* planted: transposed field table */
+#else
+    (void)n;
+    return h[i * q + v];
+#endif
+}
+
+/* q-state Potts energy, FP64 */
+double oracle_potts_energy_f64(int n, int q, const double *J, const double *h, uint64_t c)
+{
+    double pair = 0.0, field = 0.0;
+    for (int i = 0; i < n; i++) {
+        int di = digit_of(c, i, q);
+        for (int j = i + 1; j < n; j++)
+            if (same_state(di, digit_of(c, j, q))) pair += J[i * n + j];
+        field += potts_field_f64(h, n, q, i, di);
+    }
+    return pair + field;
+}
+
+/* q-state Potts energy, integer coefficients, exact in int64 */
+int64_t oracle_potts_energy_i64(int n, int q, const int32_t *J, const int32_t *h, uint64_t c)
+{
+    int64_t pair = 0, field = 0;
+    for (int i = 0; i < n; i++) {
+        int di = digit_of(c, i, q);
+        for (int j = i + 1; j < n; j++)
+            if (same_state(di, digit_of(c, j, q))) pair += J[i * n + j];
+#if ORACLE_PLANT == 14
+        field += h[di * n + i];
+#else
+        field += h[i * q + di];
+#endif
+    }
+    return pair + field;
+}
+
 /* ---- selection: first S records under the total order (E, c) ---------- */
 
 typedef struct {
@@ -214,7 +277,8 @@ typedef struct {
 } rec_t;
 
 static int g_is_int; /* set before each selection; read-only while sorting */
-static int g_qubo;   /* 0: Ising energy of Eq. (1), 1: QUBO value of Eq. (2) */
+static int g_qubo;   /* 0: Ising energy of Eq. (1), 1: QUBO value of Eq. (2), 2: Potts energy */
+static int g_potts_q; /* number of Potts states (model 2) */
 
 static int rec_less(const rec_t *a, const rec_t *b)
 {
@@ -270,12 +334,14 @@ static rec_t make_rec(int n, const void *J, const void *h, uint64_t c)
     rec_t r;
     r.c = c;
     if (g_is_int) {
-        r.ie = g_qubo ? oracle_qubo_energy_i64(n, (const int32_t *)J, (const int32_t *)h, c)
-                      : oracle_energy_i64(n, (const int32_t *)J, (const int32_t *)h, c);
+        if (g_qubo == 2) r.ie = oracle_potts_energy_i64(n, g_potts_q, (const int32_t *)J, (const int32_t *)h, c);
+        else if (g_qubo == 1) r.ie = oracle_qubo_energy_i64(n, (const int32_t *)J, (const int32_t *)h, c);
+        else r.ie = oracle_energy_i64(n, (const int32_t *)J, (const int32_t *)h, c);
         r.e = (double)r.ie;
     } else {
-        r.e = g_qubo ? oracle_qubo_energy_f64(n, (const double *)J, (const double *)h, c)
-                     : oracle_energy_f64(n, (const double *)J, (const double *)h, c);
+        if (g_qubo == 2) r.e = oracle_potts_energy_f64(n, g_potts_q, (const double *)J, (const double *)h, c);
+        else if (g_qubo == 1) r.e = oracle_qubo_energy_f64(n, (const double *)J, (const double *)h, c);
+        else r.e = oracle_energy_f64(n, (const double *)J, (const double *)h, c);
         r.ie = 0;
     }
     return r;
@@ -299,6 +365,14 @@ static int low_spectrum(int is_int, int qubo, int n, const void *J, const void *
     int free_bits = n - fixed_bits;
     if (free_bits > 62) return -1;
     uint64_t count = (uint64_t)1 << free_bits;
+    if (qubo == 2) {                   /* Potts: all q^n configurations, no fixed digits */
+        if (fixed_bits != 0 || g_potts_q < 2) return -1;
+        count = 1;
+        for (int i = 0; i < n; i++) {
+            if (count > ((uint64_t)1 << 62) / (uint64_t)g_potts_q) return -1;
+            count *= (uint64_t)g_potts_q;
+        }
+    }
     if ((uint64_t)S > count) return -1;
     if (fixed_bits > 0 && fixed_bits < 64 && (fixed_value >> fixed_bits) != 0) return -1;
     uint64_t base = fixed_bits ? (fixed_value << free_bits) : 0;
@@ -389,6 +463,36 @@ int oracle_low_spectrum_i64(int n, const int32_t *J, const int32_t *h, int S,
     rec_t *out = (rec_t *)malloc(sizeof(rec_t) * (size_t)S);
     if (!out) return -2;
     int rc = low_spectrum(1, 0, n, J, h, S, fixed_bits, fixed_value, mode, threads, out);
+    if (rc == 0)
+        for (int k = 0; k < S; k++) { out_e[k] = out[k].ie; out_c[k] = out[k].c; }
+    free(out);
+    return rc;
+}
+
+/* The S lowest (E, c) of the q-state Potts model, FP64 */
+int oracle_potts_low_spectrum_f64(int n, int q, const double *J, const double *h, int S, int mode, int threads,
+                                  double *out_e, uint64_t *out_c)
+{
+    if (S < 1 || q < 2 || q > 255) return -1;
+    rec_t *out = (rec_t *)malloc(sizeof(rec_t) * (size_t)S);
+    if (!out) return -2;
+    g_potts_q = q;
+    int rc = low_spectrum(0, 2, n, J, h, S, 0, 0, mode, threads, out);
+    if (rc == 0)
+        for (int k = 0; k < S; k++) { out_e[k] = out[k].e; out_c[k] = out[k].c; }
+    free(out);
+    return rc;
+}
+
+/* The S lowest (E, c) of the q-state Potts model, integer coefficients, exact */
+int oracle_potts_low_spectrum_i64(int n, int q, const int32_t *J, const int32_t *h, int S, int mode, int threads,
+                                  int64_t *out_e, uint64_t *out_c)
+{
+    if (S < 1 || q < 2 || q > 255) return -1;
+    rec_t *out = (rec_t *)malloc(sizeof(rec_t) * (size_t)S);
+    if (!out) return -2;
+    g_potts_q = q;
+    int rc = low_spectrum(1, 2, n, J, h, S, 0, 0, mode, threads, out);
     if (rc == 0)
         for (int k = 0; k < S; k++) { out_e[k] = out[k].ie; out_c[k] = out[k].c; }
     free(out);

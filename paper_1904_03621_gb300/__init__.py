@@ -7,9 +7,10 @@ first use and raise if it is missing.
 import importlib
 
 __all__ = ["instances", "low_spectrum", "low_spectrum_batched", "low_spectrum_backward", "low_spectrum_qubo",
-           "LowSpectrumFn", "search", "Solution", "lib"]
+           "low_spectrum_potts", "LowSpectrumFn", "search", "Solution", "lib"]
 
-_API = ("low_spectrum", "low_spectrum_batched", "low_spectrum_backward", "low_spectrum_qubo", "LowSpectrumFn")
+_API = ("low_spectrum", "low_spectrum_batched", "low_spectrum_backward", "low_spectrum_qubo", "low_spectrum_potts",
+        "LowSpectrumFn")
 
 
 def __getattr__(name):

@@ -17,7 +17,7 @@ BF_VARIANT_AUTO, BF_VARIANT_GRAY, BF_VARIANT_TC = 0, 1, 2
 # every symbol include/bf.h declares
 EXPORTS = ["bf_workspace_size", "bf_low_spectrum", "bf_low_spectrum_noalloc", "bf_batched_workspace_size",
            "bf_low_spectrum_batched", "bf_autotune_batched", "bf_low_spectrum_backward", "bf_qubo_workspace_size",
-           "bf_low_spectrum_qubo", "bf_instance_digest", "bf_cursor_bytes", "bf_cursor_init",
+           "bf_low_spectrum_qubo", "bf_potts_workspace_size", "bf_low_spectrum_potts", "bf_instance_digest", "bf_cursor_bytes", "bf_cursor_init",
            "bf_cursor_workspace_size", "bf_cursor_step", "bf_cursor_state", "bf_workspace_status",
            "bf_last_profile", "bf_launch_count", "bf_merge_lists", "bf_status_string", "bf_last_error_detail",
            "bf_version"]
@@ -70,6 +70,10 @@ def load(path: str | None = None):
     lib.bf_qubo_workspace_size.argtypes = [i32, i32, i32, ctypes.POINTER(Options)]
     lib.bf_low_spectrum_qubo.restype = i32
     lib.bf_low_spectrum_qubo.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, sz, ctypes.POINTER(Options), vp]
+    lib.bf_potts_workspace_size.restype = sz
+    lib.bf_potts_workspace_size.argtypes = [i32, i32, i32, i32, ctypes.POINTER(Options)]
+    lib.bf_low_spectrum_potts.restype = i32
+    lib.bf_low_spectrum_potts.argtypes = [vp, vp, i32, i32, i32, i32, vp, vp, vp, sz, ctypes.POINTER(Options), vp]
     lib.bf_instance_digest.restype = ctypes.c_uint64
     lib.bf_instance_digest.argtypes = [vp, vp, i32, i32]
     lib.bf_cursor_bytes.restype = sz

@@ -116,6 +116,45 @@ def low_spectrum_qubo(a: torch.Tensor, b: torch.Tensor, S: int, *, variant: int 
     return F, states
 
 
+def low_spectrum_potts(J: torch.Tensor, h: torch.Tensor, S: int, *, task_log2: int = 0, grid_blocks: int = 0,
+                       spill_log2: int = 0, profile: int = 0, stream=None, workspace: torch.Tensor | None = None,
+                       check: bool = True):
+    """S lowest (energy, configuration) pairs of the q-state Potts model.
+
+    E(sigma) = sum_{i<j} J_ij [sigma_i == sigma_j] + sum_i h_i(sigma_i), sigma_i in {0..q-1};
+    configuration c = sum_i sigma_i q^i.  J: (n, n) CUDA tensor, strict upper triangle read;
+    h: (n, q) CUDA tensor of the same dtype (q = h.shape[1], 2..8).  Returns (energies, states).
+    """
+    lib = _lib.load()
+    if J.dtype not in _DTYPES or h.dtype != J.dtype:
+        raise TypeError("J and h must share one of int32, float32, float64")
+    if not (J.is_cuda and h.is_cuda):
+        raise ValueError("J and h must be CUDA tensors")
+    if h.dim() != 2 or h.shape[0] != J.shape[0]:
+        raise ValueError("h must have shape (n, q)")
+    n, q = J.shape[0], h.shape[1]
+    J = J.contiguous()
+    h = h.contiguous()
+    o = _options(0, 0, 0, task_log2, grid_blocks, spill_log2, profile)
+    nbytes = lib.bf_potts_workspace_size(n, q, S, _DTYPES[J.dtype], ctypes.byref(o))
+    if nbytes == 0:
+        _lib.check(lib.bf_low_spectrum_potts(None, None, n, q, S, _DTYPES[J.dtype], None, None, None, 0,
+                                             ctypes.byref(o), None), lib)
+        raise _lib.BFError(_lib.BF_EINVAL, lib.bf_last_error_detail().decode())
+    if workspace is None or workspace.numel() < nbytes:
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device=J.device)
+    edt = torch.int64 if J.dtype == torch.int32 else torch.float64
+    energies = torch.empty(S, dtype=edt, device=J.device)
+    states = torch.empty(S, dtype=torch.int64, device=J.device)
+    sh = _stream_handle(stream)
+    st = lib.bf_low_spectrum_potts(J.data_ptr(), h.data_ptr(), n, q, S, _DTYPES[J.dtype], energies.data_ptr(),
+                                   states.data_ptr(), workspace.data_ptr(), workspace.numel(), ctypes.byref(o), sh)
+    _lib.check(st, lib)
+    if check:
+        _lib.check(lib.bf_workspace_status(workspace.data_ptr(), sh), lib)
+    return energies, states
+
+
 def states_u64(states: torch.Tensor) -> np.ndarray:
     """Configuration integers as numpy uint64 (the int64 tensor holds their bits)."""
     return states.detach().cpu().numpy().view(np.uint64)

@@ -1,6 +1,7 @@
 // Host side of the C ABI declared in include/bf.h: argument validation,
 // launch plan, workspace layout and the kernel sequence of one search.
 #include <algorithm>
+#include <cstddef>
 #include <atomic>
 #include <map>
 #include <mutex>
@@ -393,6 +394,176 @@ bf_status bf_low_spectrum_qubo(const void* a, const void* b, int n, int S, bf_dt
     auto* hdr = reinterpret_cast<bf::WsHeader*>(ws);
     e = bf::launch_qubo_finish(F, S, dtype == BF_I32 ? 0 : 1, ws + q.off, &hdr->status, stream);
     if (e != cudaSuccess) return cuda_fail(e, "QUBO offset");
+    return BF_OK;
+}
+
+// ---- q-state Potts model -------------------------------------------------------
+
+namespace {
+
+struct PottsPlan {
+    bool direct;
+    int B, m, grid, seg_log2, list_cap, seed_per_block, seed_blocks;
+    unsigned long long space, ntasks, seed_sample;
+    bf::Layout L;
+    size_t prep_off, bytes;
+};
+
+bf_status potts_plan(int n, int q, int S, int dtype, const bf_options* opt, PottsPlan& pl)
+{
+    bf_options o{};
+    if (opt) o = *opt;
+    if (q < bf::kPottsMinQ || q > bf::kPottsMaxQ) return fail(BF_EUNSUPPORTED, "q=%d outside [2, 8]", q);
+    if (n < 1 || n > bf::kMaxN) return fail(BF_EINVAL, "n=%d outside [1, 64]", n);
+    if (dtype != BF_I32 && dtype != BF_F32 && dtype != BF_F64) return fail(BF_EINVAL, "unknown dtype %d", dtype);
+    if (o.fixed_bits != 0 || o.variant > BF_VARIANT_GRAY) return fail(BF_EINVAL, "fixed_bits / variant not supported for the Potts model");
+    unsigned long long space = 1;
+    for (int i = 0; i < n; i++) {
+        if (space > (1ull << 62) / (unsigned long long)q) return fail(BF_EINVAL, "q^n exceeds 2^62");
+        space *= (unsigned long long)q;
+    }
+    if (S < 1) return fail(BF_EINVAL, "S=%d < 1", S);
+    if ((unsigned long long)S > space) return fail(BF_EINVAL, "S=%d exceeds q^n configurations", S);
+    if (S > BF_MAX_S) return fail(BF_EUNSUPPORTED, "S=%d exceeds BF_MAX_S=%d", S, BF_MAX_S);
+    if (o.spill_log2 < 0 || o.spill_log2 > 28) return fail(BF_EINVAL, "spill_log2=%d outside [0, 28]", o.spill_log2);
+    pl = PottsPlan{};
+    pl.space = space;
+    pl.direct = space <= 4096ull;
+    if (pl.direct) {
+        pl.bytes = sizeof(bf::WsHeader);
+        return BF_OK;
+    }
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "device query");
+    pl.list_cap = bf::list_capacity(S);
+    pl.B = bf::potts_inner_digits(q);
+    const int outer = n - pl.B;
+    const int bps = bf::potts_walk_blocks_per_sm(q, 0, n, pl.list_cap);
+    if (bps < 1) return fail(BF_EUNSUPPORTED, "Potts walk kernel does not fit on an SM (S=%d)", S);
+    pl.grid = o.grid_blocks ? o.grid_blocks : sms * bps;
+    // enough tasks for ~4 per walk slot, middle digits for the rest (per-thread tables: m q <= 24)
+    const unsigned long long want = (unsigned long long)pl.grid * 256ull * 4ull;
+    int tdig = 0;
+    for (unsigned long long c = 1; c < want && tdig < outer; c *= (unsigned long long)q) tdig++;
+    int m = outer - tdig;
+    m = std::max(0, std::min(m, bf::kPottsMidTable / q));
+    pl.m = m;
+    pl.ntasks = bf::potts_pow(q, outer - m);
+    unsigned long long nb = bf::potts_pow(q, m);
+    int lg = 0;
+    while ((2ull << lg) <= nb && lg < 4) lg++;
+    pl.seg_log2 = lg;
+    pl.seed_per_block = std::max(pl.list_cap, 2048);
+    unsigned long long sample = std::min(space, 1ull << bf::kSeedLog2);
+    sample = std::min(sample, (unsigned long long)pl.grid * pl.seed_per_block);
+    pl.seed_sample = sample;
+    pl.seed_blocks = (int)((sample + pl.seed_per_block - 1) / pl.seed_per_block);
+    pl.L = bf::make_layout(S, pl.grid, o.spill_log2 ? o.spill_log2 : 21);
+    pl.prep_off = bf::align_up(pl.L.total, 256);
+    pl.bytes = pl.prep_off + bf::align_up(sizeof(bf::PottsPrep), 256);
+    return BF_OK;
+}
+
+}  // namespace
+
+size_t bf_potts_workspace_size(int n, int q, int S, bf_dtype dtype, const bf_options* opt)
+{
+    PottsPlan pl;
+    if (potts_plan(n, q, S, dtype, opt, pl) != BF_OK) return 0;
+    return pl.bytes;
+}
+
+bf_status bf_low_spectrum_potts(const void* J, const void* h, int n, int q, int S, bf_dtype dtype, void* energies,
+                                uint64_t* states, void* workspace, size_t workspace_bytes, const bf_options* opt,
+                                void* stream_ptr)
+{
+    g_detail.clear();
+    PottsPlan pl;
+    bf_status st = potts_plan(n, q, S, dtype, opt, pl);
+    if (st != BF_OK) return st;
+    if (!J || !h || !energies || !states || !workspace) return fail(BF_EINVAL, "null pointer argument");
+    if (workspace_bytes < pl.bytes)
+        return fail(BF_EWORKSPACE, "workspace of %zu bytes < %zu required", workspace_bytes, pl.bytes);
+    if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return fail(BF_EWORKSPACE, "workspace not 256-byte aligned");
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    char* ws = static_cast<char*>(workspace);
+    auto* hdr = reinterpret_cast<bf::WsHeader*>(ws);
+    auto* out_states = reinterpret_cast<unsigned long long*>(states);
+    if (pl.direct) {
+        cudaError_t e = bf::launch_potts_direct(J, h, n, q, dtype, S, energies, out_states, hdr, stream);
+        return e == cudaSuccess ? BF_OK : cuda_fail(e, "Potts direct kernel");
+    }
+    const bf::Layout& L = pl.L;
+    auto* prep = reinterpret_cast<bf::PottsPrep*>(ws + pl.prep_off);
+    cudaError_t e = bf::launch_potts_prep(J, h, n, q, (int)dtype, prep, hdr, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "Potts prep kernel");
+    // per-instance constants become kernel parameters of the walk
+    struct { int q, status, qs, W; double delta, emax; int dT[bf::kPottsMaxSteps]; } hp;
+    static_assert(offsetof(bf::PottsPrep, dT) == 32, "PottsPrep header layout");
+    e = cudaMemcpyAsync(&hp, prep, sizeof(hp), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e, "Potts prep copy");
+    if (hp.status & bf::kErrRange) return fail(BF_EUNSUPPORTED, "instance outside the fixed-point range");
+
+    int* AE = reinterpret_cast<int*>(ws + L.listA_E);
+    auto* AC = reinterpret_cast<unsigned long long*>(ws + L.listA_C);
+    int* BE = reinterpret_cast<int*>(ws + L.listB_E);
+    auto* BC = reinterpret_cast<unsigned long long*>(ws + L.listB_C);
+    e = bf::launch_potts_seed(prep, n, q, pl.space, pl.seed_sample, pl.seed_per_block, pl.seed_blocks, L.list_cap,
+                              AE, AC, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "Potts seed kernel");
+    bool in_a = true;
+    e = merge_tree(AE, AC, BE, BC, pl.seed_blocks, L.list_cap, S, 0, hdr, stream, in_a);
+    if (e != cudaSuccess) return cuda_fail(e, "Potts seed merge");
+    e = bf::launch_set_tau(in_a ? AE : BE, S, hdr, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "Potts seed threshold");
+
+    bf::PottsParams pp{};
+    std::memcpy(pp.dT, hp.dT, sizeof(pp.dT));
+    for (int i = 0; i <= bf::kMaxN; i++) pp.qpow[i] = i <= n ? bf::potts_pow(q, i) : 0ull;
+    pp.n = n;
+    pp.q = q;
+    pp.B = pl.B;
+    pp.m = pl.m;
+    pp.ntasks = pl.ntasks;
+    pp.S = S;
+    pp.list_cap = L.list_cap;
+    pp.W = hp.W;
+    pp.seg_log2 = pl.seg_log2;
+    pp.spill_cap = L.spill_cap;
+    pp.prep = prep;
+    pp.hdr = hdr;
+    pp.list_E = AE;
+    pp.list_C = AC;
+    pp.spill_E = reinterpret_cast<int*>(ws + L.spill_E);
+    pp.spill_C = reinterpret_cast<unsigned long long*>(ws + L.spill_C);
+    const bool profile = opt && opt->profile;
+    if (profile) {
+        if (!g_prof.start) {
+            e = cudaEventCreate(&g_prof.start);
+            if (e == cudaSuccess) e = cudaEventCreate(&g_prof.stop);
+            if (e != cudaSuccess) return cuda_fail(e, "profile events");
+        }
+        g_prof.valid = false;
+        e = cudaEventRecord(g_prof.start, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "profile event");
+    }
+    e = bf::launch_potts_walk(pp, pl.grid, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "Potts walk kernel");
+    if (profile) {
+        e = cudaEventRecord(g_prof.stop, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "profile event");
+        g_prof.valid = true;
+    }
+    e = bf::launch_absorb_spill(AE, AC, pl.grid, L.list_cap, S, hp.W, pp.spill_E, pp.spill_C, L.spill_cap, hdr, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "spill absorb");
+    e = merge_tree(AE, AC, BE, BC, pl.grid, L.list_cap, S, hp.W, hdr, stream, in_a);
+    if (e != cudaSuccess) return cuda_fail(e, "merge rounds");
+    e = bf::launch_potts_finalize(in_a ? AE : BE, in_a ? AC : BC, L.list_cap, S, n, q, (int)dtype, hp.qs, J, h,
+                                  reinterpret_cast<double*>(ws + L.rescore), energies, out_states, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "Potts finalize");
     return BF_OK;
 }
 

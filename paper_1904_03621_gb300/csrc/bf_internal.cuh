@@ -172,6 +172,78 @@ struct TcParams {                   // tensor-core screening kernel (k_tc.cu)
     unsigned long long* spill_C;
 };
 
+// ---- q-state Potts model (k_potts.cu) -----------------------------------
+
+constexpr int kPottsMinQ = 2, kPottsMaxQ = 8;
+constexpr int kPottsMaxSteps = 1024;              // configurations of one inner block (q^B)
+constexpr int kPottsMidTable = 24;                // max m * q (per-thread middle-spin tables)
+
+// inner digits walked by the unrolled block for q states (q^B <= kPottsMaxSteps)
+__host__ __device__ constexpr int potts_inner_digits(int q)
+{
+    return q == 2 ? 9 : q == 3 ? 6 : q == 4 ? 5 : q == 5 ? 4 : 3;
+}
+
+__host__ __device__ constexpr unsigned long long potts_pow(int q, int e)
+{
+    unsigned long long r = 1;
+    for (int i = 0; i < e; i++) r *= (unsigned long long)q;
+    return r;
+}
+
+// q-adic valuation of t >= 1 (the digit that changes at step t of the reflected q-ary Gray code)
+__host__ __device__ constexpr int potts_qval(unsigned long long t, int q)
+{
+    int k = 0;
+    while (t % (unsigned long long)q == 0ull) { t /= (unsigned long long)q; k++; }
+    return k;
+}
+
+// digit p of the reflected q-ary Gray code of u
+__host__ __device__ constexpr int potts_gray_digit(unsigned long long u, int q, int p)
+{
+    for (int i = 0; i < p; i++) u /= (unsigned long long)q;
+    const int d = (int)(u % (unsigned long long)q);
+    return ((u / (unsigned long long)q) & 1ull) ? q - 1 - d : d;
+}
+
+struct PottsPrep {                       // written by potts_prep_kernel (device)
+    int q, status, qs, W;                // states, status bits, scale exponent, window
+    double delta, emax;
+    int dT[kPottsMaxSteps];              // inner pair-table difference of Gray step t (t >= 1)
+    int Jq[kMaxN * kMaxN];               // quantised symmetric couplings, zero diagonal
+    int hq[kMaxN * kPottsMaxQ];          // quantised fields h_i(v), row stride q
+};
+
+struct PottsParams {
+    int dT[kPottsMaxSteps];              // copy of PottsPrep::dT (kernel-parameter constants)
+    unsigned long long qpow[kMaxN + 1];  // q^i
+    int n, q, B, m;                      // spins, states, inner digits, walked middle digits
+    unsigned long long ntasks;           // q^(n - B - m)
+    int S, list_cap, W, seg_log2;
+    unsigned spill_cap;
+    int pad0;
+    const PottsPrep* prep;
+    WsHeader* hdr;
+    int* list_E;
+    unsigned long long* list_C;
+    int* spill_E;
+    unsigned long long* spill_C;
+};
+
+cudaError_t launch_potts_prep(const void* J, const void* h, int n, int q, int dtype, PottsPrep* prep,
+                              WsHeader* hdr, cudaStream_t s);
+cudaError_t launch_potts_seed(const PottsPrep* prep, int n, int q, unsigned long long space,
+                              unsigned long long sample, int per_block, int blocks, int cap, int* outE,
+                              unsigned long long* outC, cudaStream_t s);
+cudaError_t launch_potts_walk(const PottsParams& p, int grid, cudaStream_t s);
+int potts_walk_blocks_per_sm(int q, int m, int n, int list_cap);
+cudaError_t launch_potts_direct(const void* J, const void* h, int n, int q, int dtype, int S, void* energies,
+                                unsigned long long* states, WsHeader* hdr, cudaStream_t s);
+cudaError_t launch_potts_finalize(const int* E, const unsigned long long* C, int cap, int S, int n, int q,
+                                  int dtype, int qs, const void* J, const void* h, double* rescore,
+                                  void* energies, unsigned long long* states, cudaStream_t s);
+
 // ---- batched search ----------------------------------------------------
 
 constexpr int kBMinN = 10;                       // smallest n of the batched walker

@@ -1,0 +1,731 @@
+// q-state Potts spin glass: the extension to other classical spin-glass
+// models that Sec. 2 names (the Potts model of its Ref. Wu82).
+//
+// Model (sign as the library's Eq. (1)):
+//     E(sigma) = sum_{i<j} J_ij [sigma_i == sigma_j] + sum_i h_i(sigma_i),
+// sigma_i in {0, ..., q-1}, configuration integer c = sum_i sigma_i q^i (the
+// base-q digits, generalising the binary coding of Sec. 3, Eq. (4)).  For
+// q = 2, [s_i == s_j] = (1 + s_i s_j) / 2 and the model is an Ising instance.
+//
+// Digit layout of c:
+//   [0, B)         inner digits: one fully unrolled block of q^B configurations
+//                  in reflected q-ary Gray order (one digit changes by +-1 per step)
+//   [B, B+m)       middle digits: walked in the same order, one change per block
+//   [B+m, n)       task index (base q)
+// Inside a block (outer digits o fixed):
+//     E(x) = E_base(o) + sum_{k<B} (f_k(x_k) - f_k(0)) + T[x] - T[0],
+//     f_k(v) = h_k(v) + sum_{l >= B} J_kl [v == sigma_l],
+//     T[x] = sum_{k<k'<B} J_kk' [x_k == x_k'] ,
+// so a step changing digit k from a to a +- 1 adds +-G_k(min(a, a')) + dT_t with
+// G_k(v) = f_k(v+1) - f_k(v) (registers) and dT_t = T[x_t] - T[x_{t-1}] (kernel
+// parameters): one IADD3 per configuration, a 3-input minimum per two.  A
+// middle-digit change p: a -> a' shifts E_base by C_p(a') - C_p(a) + h_p(a') -
+// h_p(a) (C_p(v) = sum_{l != p} J_pl [sigma_l == v], inner digits at 0) and
+// updates four G entries per inner digit and two C entries per other middle
+// digit (per-thread tables in shared memory).
+//
+// Arithmetic: exact int32 fixed point as for the Ising search (scale 2^qs,
+// |E_q| <= 2^29, residual bound delta, window W, FP64 rescoring of float
+// instances).  Selection, segments and the spill area follow gray_kernel.
+#include <cfloat>
+#include <climits>
+#include <type_traits>
+#include <utility>
+
+#include "bf_internal.cuh"
+#include "bf_sort.cuh"
+
+namespace bf {
+namespace {
+
+constexpr int kPottsThreads = 256;
+constexpr int kPottsPrepThreads = 256;
+constexpr int kPottsEmqLog2 = 29;
+
+__device__ __forceinline__ double load_val(const void* p, int dtype, size_t idx)
+{
+    if (dtype == 0) return (double)static_cast<const int*>(p)[idx];
+    if (dtype == 1) return (double)static_cast<const float*>(p)[idx];
+    return static_cast<const double*>(p)[idx];
+}
+
+__device__ double block_sum_d(double v, double* red)
+{
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+// ---- prep: quantisation, residual bound, inner pair-table steps ----------------
+
+__global__ void __launch_bounds__(kPottsPrepThreads) potts_prep_kernel(const void* J, const void* h, int n, int q,
+                                                                       int dtype, PottsPrep* out, WsHeader* hdr)
+{
+    __shared__ double red[kPottsPrepThreads];
+    __shared__ double s_Jd[kMaxN * kMaxN];
+    __shared__ int s_q, s_status;
+    __shared__ double s_emax;
+    const int tid = threadIdx.x;
+    const int B = potts_inner_digits(q);
+    for (int idx = tid; idx < n * n; idx += blockDim.x) {
+        const int i = idx / n, j = idx % n;
+        s_Jd[idx] = i < j ? load_val(J, dtype, idx) : 0.0;
+    }
+    __syncthreads();
+    // emax = sum_{i<j} |J_ij| + sum_i max_v |h_i(v)| bounds |E| and every field difference / 2
+    double part = 0.0;
+    for (int idx = tid; idx < n * n; idx += blockDim.x) part += fabs(s_Jd[idx]);
+    for (int i = tid; i < n; i += blockDim.x) {
+        double mx = 0.0;
+        for (int v = 0; v < q; v++) mx = fmax(mx, fabs(load_val(h, dtype, (size_t)i * q + v)));
+        part += mx;
+    }
+    const double emax = block_sum_d(part, red);
+    if (tid == 0) {
+        int status = 0, qs = 0;
+        if (emax > 0.0) {
+            int e;
+            frexp(emax, &e);                    // emax < 2^e
+            qs = kPottsEmqLog2 - e;
+            if (dtype == 0) {
+                if (qs < 0) status |= kErrRange;
+                if (qs > 16) qs = 16;
+                if (qs < 0) qs = 0;
+            } else {
+                if (qs > 200) qs = 200;
+                if (qs < -200) qs = -200;
+            }
+        }
+        if (!(emax < 1e300)) status |= kErrRange;
+        s_q = qs;
+        s_status = status;
+        s_emax = emax;
+    }
+    __syncthreads();
+    const int qs = s_q;
+    // quantise (symmetric, zero diagonal) and accumulate the residual bound
+    part = 0.0;
+    for (int idx = tid; idx < n * n; idx += blockDim.x) {
+        const int i = idx / n, j = idx % n;
+        const int a = i < j ? i : j, b = i < j ? j : i;
+        int v = 0;
+        if (a != b) {
+            const double x = s_Jd[a * n + b];
+            const double r = rint(ldexp(x, qs));
+            v = (int)r;
+            if (i < j) part += fabs(x - ldexp(r, -qs));
+        }
+        out->Jq[idx] = v;
+    }
+    for (int i = tid; i < n; i += blockDim.x) {
+        double mx = 0.0;
+        for (int v = 0; v < q; v++) {
+            const double x = load_val(h, dtype, (size_t)i * q + v);
+            const double r = rint(ldexp(x, qs));
+            out->hq[i * q + v] = (int)r;
+            mx = fmax(mx, fabs(x - ldexp(r, -qs)));
+        }
+        part += mx;
+    }
+    const double delta = block_sum_d(part, red);
+    __syncthreads();
+    // dT_t = T[x_t] - T[x_{t-1}] over the inner Gray block (needs Jq: written above by this block)
+    const int P = (int)potts_pow(q, B);
+    for (int t = tid; t < kPottsMaxSteps; t += blockDim.x) {
+        int d = 0;
+        if (t >= 1 && t < P && n >= B) {
+            int T1 = 0, T0 = 0;
+            for (int k = 0; k < B; k++)
+                for (int k2 = k + 1; k2 < B; k2++) {
+                    const int jv = out->Jq[k * n + k2];
+                    if (potts_gray_digit(t, q, k) == potts_gray_digit(t, q, k2)) T1 += jv;
+                    if (potts_gray_digit(t - 1, q, k) == potts_gray_digit(t - 1, q, k2)) T0 += jv;
+                }
+            d = T1 - T0;
+        }
+        out->dT[t] = d;
+    }
+    if (tid == 0) {
+        int status = s_status;
+        int W = 0;
+        if (dtype != 0 && delta > 0.0) {
+            const double eps = 8.0 * (double)n * (double)n * ldexp(1.0, -53) * s_emax;
+            double w = ceil(ldexp(2.0 * delta + 2.0 * eps, qs)) + 2.0;
+            if (w > (double)(1 << 28)) { w = (double)(1 << 28); status |= kErrRange; }
+            W = (int)w;
+        }
+        out->q = q;
+        out->status = status;
+        out->qs = qs;
+        out->W = W;
+        out->delta = delta;
+        out->emax = s_emax;
+        hdr->tau = INT_MAX;
+        hdr->status = (unsigned)status;
+        hdr->task_next = 0ull;
+        hdr->spill_count = 0u;
+    }
+}
+
+// exact quantised energy of configuration c (digits in base q)
+__device__ int potts_energy_q(const int* Jq, const int* hq, int n, int q, unsigned long long c)
+{
+    unsigned char d[kMaxN];
+    for (int i = 0; i < n; i++) {
+        d[i] = (unsigned char)(c % (unsigned long long)q);
+        c /= (unsigned long long)q;
+    }
+    unsigned e = 0u;
+    for (int i = 0; i < n; i++) {
+        e += (unsigned)hq[i * q + d[i]];
+        const int* Ji = Jq + i * n;
+        for (int j = i + 1; j < n; j++)
+            if (d[i] == d[j]) e += (unsigned)Ji[j];
+    }
+    return (int)e;
+}
+
+// ---- seed: exact energies of a hashed sample -------------------------------------
+
+constexpr int kPottsSeedThreads = 512;
+
+__global__ void __launch_bounds__(kPottsSeedThreads) potts_seed_kernel(const PottsPrep* prep, int n, int q,
+                                                                       unsigned long long space,
+                                                                       unsigned long long sample, int per_block,
+                                                                       int cap, int* outE, unsigned long long* outC)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned long long* C = reinterpret_cast<unsigned long long*>(smem);
+    int* E = reinterpret_cast<int*>(C + per_block);
+    int* Jq = E + per_block;
+    int* hq = Jq + n * n;
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) Jq[i] = prep->Jq[i];
+    for (int i = threadIdx.x; i < n * q; i += blockDim.x) hq[i] = prep->hq[i];
+    __syncthreads();
+    const bool full = sample >= space;        // whole space sampled: plain enumeration
+    for (int k = threadIdx.x; k < per_block; k += blockDim.x) {
+        const unsigned long long x = (unsigned long long)blockIdx.x * per_block + k;
+        if (x >= sample || x >= space) { E[k] = kEmptyE; C[k] = kEmptyC; continue; }
+        unsigned long long c = x;
+        if (!full) {
+            // splitmix64 of x, scaled onto [0, space)
+            unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            z ^= z >> 31;
+            c = __umul64hi(z, space);
+        }
+        E[k] = potts_energy_q(Jq, hq, n, q, c);
+        C[k] = c;
+    }
+    block_sort(E, C, per_block);
+    for (int i = threadIdx.x; i < cap; i += blockDim.x) {
+        outE[(size_t)blockIdx.x * cap + i] = i < per_block ? E[i] : kEmptyE;
+        outC[(size_t)blockIdx.x * cap + i] = i < per_block ? C[i] : kEmptyC;
+    }
+}
+
+// ---- the walk ------------------------------------------------------------------
+
+struct PottsSmem {
+    int* Jq;                  // n*n
+    int* hq;                  // n*q
+    int* Gt;                  // [B*(Q-1)][threads]: G_k(v) of each thread's walk
+    int* Ct;                  // [m*Q][threads]: C_p(v) of each thread's middle digits
+    int* E;                   // 2*cap
+    unsigned long long* C;    // 2*cap
+};
+
+template <int Q, int B, int t>
+__device__ __forceinline__ void potts_step(unsigned& E, unsigned& e1, int& mn, const int (&G)[B][Q - 1],
+                                           const PottsParams& p)
+{
+    constexpr int k = potts_qval(t, Q);
+    constexpr int a0 = potts_gray_digit(t - 1, Q, k), a1 = potts_gray_digit(t, Q, k);
+    constexpr bool up = a1 > a0;
+    constexpr int v = up ? a0 : a1;
+    E += (up ? (unsigned)G[k][v] : 0u - (unsigned)G[k][v]) + (unsigned)p.dT[t];
+    if constexpr ((t & 1) != 0) {
+        e1 = E;
+    } else {
+        mn = __vimin3_s32(mn, (int)e1, (int)E);
+    }
+}
+
+template <int Q, int B, int... Ts>
+__device__ __forceinline__ void potts_block(unsigned& E, unsigned& e1, int& mn, const int (&G)[B][Q - 1],
+                                            const PottsParams& p, std::integer_sequence<int, Ts...>)
+{
+    (potts_step<Q, B, Ts + 1>(E, e1, mn, G, p), ...);
+}
+
+__device__ __forceinline__ void potts_record(const PottsParams& p, const PottsSmem& s, unsigned* buf_count, int e,
+                                             unsigned long long c)
+{
+    const unsigned slot = atomicAdd(buf_count, 1u);
+    if (slot < (unsigned)p.list_cap) {
+        s.E[p.list_cap + slot] = e;
+        s.C[p.list_cap + slot] = c;
+        return;
+    }
+    const unsigned g = atomicAdd(&p.hdr->spill_count, 1u);
+    if (g < p.spill_cap) {
+        p.spill_E[g] = e;
+        p.spill_C[g] = c;
+    } else {
+        atomicOr(&p.hdr->status, kErrSpill);
+    }
+}
+
+template <int Q>
+__global__ void __launch_bounds__(kPottsThreads, 2) potts_walk_kernel(const __grid_constant__ PottsParams p)
+{
+    constexpr int B = potts_inner_digits(Q);
+    constexpr int P = (int)potts_pow(Q, B);
+    constexpr int NG = B * (Q - 1);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = p.n, m = p.m, cap = p.list_cap;
+    PottsSmem s;
+    s.C = reinterpret_cast<unsigned long long*>(smem_raw);
+    s.E = reinterpret_cast<int*>(s.C + 2 * cap);
+    s.Gt = s.E + 2 * cap;
+    s.Ct = s.Gt + NG * kPottsThreads;
+    s.Jq = s.Ct + kPottsMidTable * kPottsThreads;
+    s.hq = s.Jq + n * n;
+
+    __shared__ unsigned s_buf_count;
+    __shared__ int s_list_count, s_kE;
+    __shared__ unsigned long long s_batch, s_kC;
+
+    const int tid = threadIdx.x;
+    const PottsPrep* prep = p.prep;
+    for (int i = tid; i < n * n; i += blockDim.x) s.Jq[i] = prep->Jq[i];
+    for (int i = tid; i < n * Q; i += blockDim.x) s.hq[i] = prep->hq[i];
+    if (tid == 0) {
+        s_buf_count = 0u;
+        s_list_count = 0;
+        s_kE = kEmptyE;
+        s_kC = kEmptyC;
+    }
+    __syncthreads();
+
+    const int S = p.S, W = p.W;
+    const unsigned long long nblocks = p.qpow[m];
+    const unsigned long long seg_mask = (1ull << p.seg_log2) - 1ull;
+    const unsigned long long task_mul = p.qpow[B + m];
+    int* Gt = s.Gt + tid;                          // entry e at Gt[e * kPottsThreads]
+    int* Ct = s.Ct + tid;
+
+    int tau_scr = 0, tie_E = kEmptyE;
+    unsigned long long tie_C = kEmptyC;
+    auto refresh = [&]() {
+        const int tg = *(volatile int*)&p.hdr->tau;
+        const int t = min(s_kE, tg);
+        tie_E = (W == 0) ? s_kE : kEmptyE;
+        tie_C = s_kC;
+        long long ts = (long long)t + W;
+        if (ts > (1ll << 30)) ts = 1ll << 30;
+        tau_scr = (int)ts;
+    };
+    refresh();
+
+    for (;;) {
+        if (tid == 0) s_batch = atomicAdd(&p.hdr->task_next, (unsigned long long)kPottsThreads);
+        __syncthreads();
+        const unsigned long long base = s_batch;
+        __syncthreads();
+        if (base >= p.ntasks) break;
+        unsigned long long task = base + (unsigned long long)tid;
+        const bool active = task < p.ntasks;
+        if (!active) task = 0;                      // a valid walk whose hits are ignored
+        const unsigned long long c0 = task * task_mul;
+
+        // ---- state at the start of the task (inner and middle digits 0)
+        unsigned Ebase;
+        {
+            unsigned char d[kMaxN];
+            unsigned long long x = c0;
+            for (int i = 0; i < n; i++) {
+                d[i] = (unsigned char)(x % (unsigned long long)Q);
+                x /= (unsigned long long)Q;
+            }
+            unsigned e = 0u;
+            for (int i = 0; i < n; i++) {
+                e += (unsigned)s.hq[i * Q + d[i]];
+                for (int j = i + 1; j < n; j++)
+                    if (d[i] == d[j]) e += (unsigned)s.Jq[i * n + j];
+            }
+            Ebase = e;
+            // G_k(v) = f_k(v+1) - f_k(v), f_k(v) = h_k(v) + sum_{l >= B} J_kl [v == d_l]
+            for (int k = 0; k < B; k++) {
+                int f[Q];
+#pragma unroll
+                for (int v = 0; v < Q; v++) f[v] = s.hq[k * Q + v];
+                for (int l = B; l < n; l++) {
+                    const int jv = s.Jq[k * n + l];
+#pragma unroll
+                    for (int v = 0; v < Q; v++) f[v] += (d[l] == v) ? jv : 0;
+                }
+#pragma unroll
+                for (int v = 0; v < Q - 1; v++) Gt[(k * (Q - 1) + v) * kPottsThreads] = f[v + 1] - f[v];
+            }
+            // C_p(v) = sum_{l != B+p} J_{B+p, l} [d_l == v] for the middle digits
+            for (int pm = 0; pm < m; pm++) {
+                const int sp = B + pm;
+                int cv[Q];
+#pragma unroll
+                for (int v = 0; v < Q; v++) cv[v] = 0;
+                for (int l = 0; l < n; l++) {
+                    if (l == sp) continue;
+                    const int jv = s.Jq[sp * n + l];
+#pragma unroll
+                    for (int v = 0; v < Q; v++) cv[v] += (d[l] == v) ? jv : 0;
+                }
+#pragma unroll
+                for (int v = 0; v < Q; v++) Ct[(pm * Q + v) * kPottsThreads] = cv[v];
+            }
+        }
+
+        for (unsigned long long u = 0; u < nblocks; ++u) {
+            // ---- one block of q^B configurations
+            int G[B][Q - 1];
+#pragma unroll
+            for (int k = 0; k < B; k++)
+#pragma unroll
+                for (int v = 0; v < Q - 1; v++) G[k][v] = Gt[(k * (Q - 1) + v) * kPottsThreads];
+            unsigned E = Ebase, e1 = Ebase;
+            int mn = (int)Ebase;
+            potts_block<Q, B>(E, e1, mn, G, p, std::make_integer_sequence<int, P - 1>{});
+            mn = min(mn, (int)e1);
+            if (active && mn <= tau_scr) {
+                // exact rescan of the block
+                unsigned long long mid = 0ull;
+                for (int pm = 0; pm < m; pm++) mid += (unsigned long long)potts_gray_digit(u, Q, pm) * p.qpow[pm];
+                const unsigned long long cb = c0 + mid * p.qpow[B];
+                unsigned e = Ebase;
+                unsigned long long x = 0ull;
+                for (int t = 0; t < P; t++) {
+                    if (t > 0) {
+                        const int k = potts_qval((unsigned long long)t, Q);
+                        const int a0 = potts_gray_digit((unsigned long long)(t - 1), Q, k);
+                        const int a1 = potts_gray_digit((unsigned long long)t, Q, k);
+                        const bool up = a1 > a0;
+                        const unsigned g = (unsigned)Gt[(k * (Q - 1) + (up ? a0 : a1)) * kPottsThreads];
+                        e += (up ? g : 0u - g) + (unsigned)p.dT[t];
+                        x = up ? x + p.qpow[k] : x - p.qpow[k];
+                    }
+                    const int ei = (int)e;
+                    const unsigned long long c = cb + x;
+                    if (ei <= tau_scr && !(ei == tie_E && c > tie_C)) potts_record(p, s, &s_buf_count, ei, c);
+                }
+            }
+
+            // ---- segment boundary: merge the buffer into the block list
+            if ((u & seg_mask) == seg_mask || u < 16ull || u + 1 == nblocks) {
+                __syncthreads();
+                const unsigned bc = s_buf_count;
+                __syncthreads();
+                if (bc > 0u) {
+                    const int lc = s_list_count;
+                    const int nb = bc < (unsigned)cap ? (int)bc : cap;
+                    for (int i = tid; i < 2 * cap; i += blockDim.x) {
+                        if ((i >= lc && i < cap) || i >= cap + nb) {
+                            s.E[i] = kEmptyE;
+                            s.C[i] = kEmptyC;
+                        }
+                    }
+                    block_sort(s.E, s.C, 2 * cap);
+                    if (tid == 0) {
+                        const int total = lc + nb;
+                        int keep = total;
+                        if (total >= S) {
+                            const int K = s.E[S - 1];
+                            keep = S;
+                            if (W > 0) {
+                                const long long lim = (long long)K + W;
+                                keep = upper_bound_key(s.E, 2 * cap, lim > INT_MAX - 1 ? INT_MAX - 1 : (int)lim);
+                                if (keep > total) keep = total;
+                                if (keep > cap) { keep = cap; atomicOr(&p.hdr->status, kErrWindow); }
+                            }
+                            s_kE = K;
+                            s_kC = s.C[S - 1];
+                            atomicMin(&p.hdr->tau, K);
+                        } else if (keep > cap) {
+                            keep = cap;
+                        }
+                        s_list_count = keep;
+                        s_buf_count = 0u;
+                    }
+                    __syncthreads();
+                }
+                refresh();
+            }
+
+            // ---- change one middle digit: pm = q-adic valuation of u + 1, a -> a'
+            if (u + 1 < nblocks) {
+                const int pm = potts_qval(u + 1, Q);
+                const int a = potts_gray_digit(u, Q, pm), a2 = potts_gray_digit(u + 1, Q, pm);
+                const int sp = B + pm;
+                Ebase += (unsigned)(Ct[(pm * Q + a2) * kPottsThreads] - Ct[(pm * Q + a) * kPottsThreads]) +
+                         (unsigned)(s.hq[sp * Q + a2] - s.hq[sp * Q + a]);
+                for (int k = 0; k < B; k++) {
+                    const int jv = s.Jq[k * n + sp];
+                    int* g = Gt + k * (Q - 1) * kPottsThreads;
+                    // f_k(a) -= J, f_k(a2) += J
+                    if (a >= 1) g[(a - 1) * kPottsThreads] -= jv;
+                    if (a <= Q - 2) g[a * kPottsThreads] += jv;
+                    if (a2 >= 1) g[(a2 - 1) * kPottsThreads] += jv;
+                    if (a2 <= Q - 2) g[a2 * kPottsThreads] -= jv;
+                }
+                for (int p2 = 0; p2 < m; p2++) {
+                    if (p2 == pm) continue;
+                    const int jv = s.Jq[(B + p2) * n + sp];
+                    Ct[(p2 * Q + a) * kPottsThreads] -= jv;
+                    Ct[(p2 * Q + a2) * kPottsThreads] += jv;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const int lc = s_list_count;
+    for (int i = tid; i < cap; i += blockDim.x) {
+        p.list_E[(size_t)blockIdx.x * cap + i] = i < lc ? s.E[i] : kEmptyE;
+        p.list_C[(size_t)blockIdx.x * cap + i] = i < lc ? s.C[i] : kEmptyC;
+    }
+}
+
+size_t potts_walk_smem(int q, int n, int list_cap)
+{
+    const int B = potts_inner_digits(q);
+    return (size_t)2 * list_cap * 12 + (size_t)B * (q - 1) * kPottsThreads * 4 +
+           (size_t)kPottsMidTable * kPottsThreads * 4 + (size_t)n * n * 4 + (size_t)n * q * 4;
+}
+
+template <int Q>
+const void* walk_fn()
+{
+    return reinterpret_cast<const void*>(&potts_walk_kernel<Q>);
+}
+
+const void* walk_for(int q)
+{
+    switch (q) {
+    case 2: return walk_fn<2>();
+    case 3: return walk_fn<3>();
+    case 4: return walk_fn<4>();
+    case 5: return walk_fn<5>();
+    case 6: return walk_fn<6>();
+    case 7: return walk_fn<7>();
+    default: return walk_fn<8>();
+    }
+}
+
+// ---- FP64 rescoring and direct enumeration -----------------------------------
+
+// Potts energy in FP64 from the caller's J and h, one warp per record
+__global__ void __launch_bounds__(256) potts_rescore_kernel(const int* E, const unsigned long long* C, int cap,
+                                                            int n, int q, int dtype, const void* J, const void* h,
+                                                            double* out)
+{
+    __shared__ unsigned char dig[8][kMaxN];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int r = warp; r < cap; r += nwarps) {
+        const bool empty = E[r] == kEmptyE;
+        if (!empty && lane == 0) {
+            unsigned long long c = C[r];
+            for (int i = 0; i < n; i++) {
+                dig[wib][i] = (unsigned char)(c % (unsigned long long)q);
+                c /= (unsigned long long)q;
+            }
+        }
+        __syncwarp();
+        double part = 0.0;
+        if (!empty) {
+            for (int i = lane; i < n; i += 32) {
+                const int di = dig[wib][i];
+                double row = load_val(h, dtype, (size_t)i * q + di);
+                for (int j = i + 1; j < n; j++)
+                    if (dig[wib][j] == di) row += load_val(J, dtype, (size_t)i * n + j);
+                part += row;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (lane == 0) out[r] = empty ? DBL_MAX : part;
+        __syncwarp();
+    }
+}
+
+constexpr int kPottsDirectThreads = 512;
+
+template <typename K>
+__global__ void __launch_bounds__(kPottsDirectThreads) potts_direct_kernel(const void* J, const void* h, int n, int q,
+                                                                          int dtype, int R, int S, void* energies,
+                                                                          unsigned long long* states)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    K* key = reinterpret_cast<K*>(smem);
+    unsigned long long* cfg = reinterpret_cast<unsigned long long*>(key + R);
+    const int space = (int)potts_pow(q, n);
+    for (int x = threadIdx.x; x < R; x += blockDim.x) {
+        if (x >= space) {
+            if constexpr (std::is_same<K, double>::value) key[x] = DBL_MAX;
+            else key[x] = LLONG_MAX;
+            cfg[x] = kEmptyC;
+            continue;
+        }
+        unsigned char d[kMaxN];
+        int y = x;
+        for (int i = 0; i < n; i++) {
+            d[i] = (unsigned char)(y % q);
+            y /= q;
+        }
+        K e = 0;
+        for (int i = 0; i < n; i++) {
+            e += (K)load_val(h, dtype, (size_t)i * q + d[i]);
+            for (int j = i + 1; j < n; j++)
+                if (d[i] == d[j]) e += (K)load_val(J, dtype, (size_t)i * n + j);
+        }
+        key[x] = e;
+        cfg[x] = (unsigned long long)x;
+    }
+    block_sort(key, cfg, R);
+    for (int k = threadIdx.x; k < S; k += blockDim.x) {
+        static_cast<K*>(energies)[k] = key[k];
+        states[k] = cfg[k];
+    }
+}
+
+__global__ void potts_finalize_int_kernel(const int* E, const unsigned long long* C, int S, int qs, long long* out,
+                                          unsigned long long* states)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < S; k += gridDim.x * blockDim.x) {
+        out[k] = (long long)(E[k] >> qs);
+        states[k] = C[k];
+    }
+}
+
+__global__ void __launch_bounds__(512) potts_sort_rescored_kernel(const unsigned long long* C, const double* E64,
+                                                                  int cap, int S, double* energies,
+                                                                  unsigned long long* states)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned long long* cfg = reinterpret_cast<unsigned long long*>(smem);
+    double* key = reinterpret_cast<double*>(cfg + cap);
+    for (int i = threadIdx.x; i < cap; i += blockDim.x) {
+        key[i] = E64[i];
+        cfg[i] = C[i];
+    }
+    block_sort(key, cfg, cap);
+    for (int k = threadIdx.x; k < S; k += blockDim.x) {
+        energies[k] = key[k];
+        states[k] = cfg[k];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_potts_prep(const void* J, const void* h, int n, int q, int dtype, PottsPrep* prep, WsHeader* hdr,
+                              cudaStream_t s)
+{
+    potts_prep_kernel<<<1, kPottsPrepThreads, 0, s>>>(J, h, n, q, dtype, prep, hdr);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_potts_seed(const PottsPrep* prep, int n, int q, unsigned long long space,
+                              unsigned long long sample, int per_block, int blocks, int cap, int* outE,
+                              unsigned long long* outC, cudaStream_t s)
+{
+    const size_t smem = (size_t)per_block * 12 + (size_t)n * n * 4 + (size_t)n * q * 4;
+    cudaError_t e = cudaFuncSetAttribute(potts_seed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    potts_seed_kernel<<<blocks, kPottsSeedThreads, smem, s>>>(prep, n, q, space, sample, per_block, cap, outE, outC);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+int potts_walk_blocks_per_sm(int q, int m, int n, int list_cap)
+{
+    (void)m;
+    const void* fn = walk_for(q);
+    const size_t smem = potts_walk_smem(q, n, list_cap);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    int bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kPottsThreads, smem) != cudaSuccess) return 0;
+    return bps;
+}
+
+cudaError_t launch_potts_walk(const PottsParams& p, int grid, cudaStream_t s)
+{
+    const size_t smem = potts_walk_smem(p.q, p.n, p.list_cap);
+    const void* fn = walk_for(p.q);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    switch (p.q) {
+    case 2: potts_walk_kernel<2><<<grid, kPottsThreads, smem, s>>>(p); break;
+    case 3: potts_walk_kernel<3><<<grid, kPottsThreads, smem, s>>>(p); break;
+    case 4: potts_walk_kernel<4><<<grid, kPottsThreads, smem, s>>>(p); break;
+    case 5: potts_walk_kernel<5><<<grid, kPottsThreads, smem, s>>>(p); break;
+    case 6: potts_walk_kernel<6><<<grid, kPottsThreads, smem, s>>>(p); break;
+    case 7: potts_walk_kernel<7><<<grid, kPottsThreads, smem, s>>>(p); break;
+    default: potts_walk_kernel<8><<<grid, kPottsThreads, smem, s>>>(p); break;
+    }
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_potts_direct(const void* J, const void* h, int n, int q, int dtype, int S, void* energies,
+                                unsigned long long* states, WsHeader* hdr, cudaStream_t s)
+{
+    const int space = (int)potts_pow(q, n);
+    int R = 1;
+    while (R < space) R <<= 1;
+    const size_t smem = (size_t)R * 16;
+    cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), s);
+    if (e != cudaSuccess) return e;
+    if (dtype == 0) {
+        e = cudaFuncSetAttribute(potts_direct_kernel<long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        potts_direct_kernel<long long><<<1, kPottsDirectThreads, smem, s>>>(J, h, n, q, dtype, R, S, energies,
+                                                                           states);
+    } else {
+        e = cudaFuncSetAttribute(potts_direct_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        potts_direct_kernel<double><<<1, kPottsDirectThreads, smem, s>>>(J, h, n, q, dtype, R, S, energies, states);
+    }
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_potts_finalize(const int* E, const unsigned long long* C, int cap, int S, int n, int q, int dtype,
+                                  int qs, const void* J, const void* h, double* rescore, void* energies,
+                                  unsigned long long* states, cudaStream_t s)
+{
+    if (dtype == 0) {
+        potts_finalize_int_kernel<<<(S + 255) / 256, 256, 0, s>>>(E, C, S, qs, static_cast<long long*>(energies),
+                                                                  states);
+        count_launches(1);
+        return cudaGetLastError();
+    }
+    potts_rescore_kernel<<<(cap + 7) / 8, 256, 0, s>>>(E, C, cap, n, q, dtype, J, h, rescore);
+    count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem = (size_t)cap * 16;
+    e = cudaFuncSetAttribute(potts_sort_rescored_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    potts_sort_rescored_kernel<<<1, 512, smem, s>>>(C, rescore, cap, S, static_cast<double*>(energies), states);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace bf

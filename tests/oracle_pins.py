@@ -369,8 +369,77 @@ def pin_qubo_separable(o):
     assert c[1] == mask ^ (1 << k) and abs(f[1] - (f[0] + abs(b[k]))) < 1e-12
 
 
+def pin_potts_q2_is_ising(o):
+    """q = 2 Potts model (Sec. 2's extension to other classical models) against the Ising
+    oracle: [s_i == s_j] = (1 + s_i s_j) / 2 and h_i(v) splits into its mean and its half
+    difference, so E_P(c) = E_I(c; J/2, (h_i(1) - h_i(0)) / 2) + sum_{i<j} J_ij / 2 +
+    sum_i (h_i(0) + h_i(1)) / 2 for every configuration (same bit encoding)."""
+    rng = np.random.default_rng(31)
+    n = 11
+    J = rng.standard_normal((n, n))
+    hp = rng.standard_normal((n, 2))
+    U = np.triu(J, 1)
+    e_i = o.all_energies(U / 2.0, (hp[:, 1] - hp[:, 0]) / 2.0)
+    const = U.sum() / 2.0 + hp.sum() / 2.0
+    for c in range(1 << n):
+        assert abs(o.potts_energy(J, hp, c) - (e_i[c] + const)) < 1e-10, c
+    e_p, c_p = o.potts_low_spectrum(J, hp, 30)
+    e_s, c_s = o.low_spectrum(U / 2.0, (hp[:, 1] - hp[:, 0]) / 2.0, 30)
+    assert np.array_equal(c_p, c_s) and np.abs(e_p - (e_s + const)).max() < 1e-10
+
+
+def pin_potts_ferromagnet(o):
+    """J_ij = -1, h = 0: the q uniform configurations c = v (q^n - 1) / (q - 1) are the ground
+    states with E = -n(n-1)/2; the next level, one spin different, has E = -(n-1)(n-2)/2 and
+    multiplicity n q (q - 1)."""
+    for n, q in ((6, 3), (5, 4)):
+        J = -np.ones((n, n), dtype=np.int32)
+        h = np.zeros((n, q), dtype=np.int32)
+        k = q + n * q * (q - 1)
+        e, c = o.potts_low_spectrum(J, h, k + 1)
+        rep = (q ** n - 1) // (q - 1)
+        assert list(c[:q]) == [v * rep for v in range(q)]
+        assert all(e[:q] == -n * (n - 1) // 2)
+        assert all(e[q:k] == -(n - 1) * (n - 2) // 2)
+        assert e[k] > e[k - 1]
+
+
+def pin_potts_fields_only(o):
+    """J = 0: E = sum_i h_i(sigma_i) is separable; the ground state takes argmin_v h_i(v)
+    per spin and the next state changes the spin with the smallest second-best gap."""
+    rng = np.random.default_rng(32)
+    n, q = 7, 3
+    h = rng.standard_normal((n, q))
+    J = np.zeros((n, n))
+    e, c = o.potts_low_spectrum(J, h, 2)
+    best = h.argmin(axis=1)
+    assert c[0] == sum(int(best[i]) * q ** i for i in range(n))
+    assert abs(e[0] - h.min(axis=1).sum()) < 1e-12
+    srt = np.sort(h, axis=1)
+    gaps = srt[:, 1] - srt[:, 0]
+    assert abs(e[1] - (e[0] + gaps.min())) < 1e-12
+
+
+def pin_potts_relabel_and_sum(o):
+    """h = 0: a global relabelling of the q states leaves E unchanged.  With fields: the sum of
+    E over all q^n configurations is q^(n-1) (sum_{i<j} J_ij + sum_{i,v} h_i(v))."""
+    rng = np.random.default_rng(33)
+    n, q = 6, 3
+    J = rng.integers(-5, 6, (n, n)).astype(np.int32)
+    h0 = np.zeros((n, q), dtype=np.int32)
+    perm = [2, 0, 1]
+    for c in rng.integers(0, q ** n, 40):
+        d = [(int(c) // q ** i) % q for i in range(n)]
+        c2 = sum(perm[d[i]] * q ** i for i in range(n))
+        assert o.potts_energy(J, h0, int(c)) == o.potts_energy(J, h0, c2)
+    h = rng.integers(-5, 6, (n, q)).astype(np.int32)
+    total = sum(o.potts_energy(J, h, c) for c in range(q ** n))
+    assert total == q ** (n - 1) * (int(np.triu(J, 1).sum()) + int(h.sum()))
+
+
 ALL_PINS = [
     pin_paper_example, pin_coding_example, pin_ferromagnet, pin_fields_only, pin_z2, pin_gauge,
     pin_qubo, pin_sum_zero, pin_matrix_form, pin_full_sort, pin_ties, pin_streaming_equals_sort,
     pin_subspace, pin_grad, pin_qubo_closed_forms, pin_qubo_ising_map, pin_qubo_separable,
+    pin_potts_q2_is_ising, pin_potts_ferromagnet, pin_potts_fields_only, pin_potts_relabel_and_sum,
 ]

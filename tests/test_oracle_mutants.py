@@ -4,7 +4,8 @@ This shows the pins are sensitive to the plausible errors they guard
 against: a dropped field term, a flipped sign, the wrong triangle of J, the
 diagonal included, reversed or inverted bit encoding, reversed tie order, a
 lost record, a wrong gradient factor, single-precision accumulation and, for the
-QUBO form, the diagonal or the lower triangle of a read.
+QUBO form, the diagonal or the lower triangle of a read, and for the Potts model an
+inverted pair indicator or a transposed field table.
 """
 import pytest
 
@@ -24,6 +25,8 @@ PLANTS = {
     10: "energy accumulated in single precision",
     11: "QUBO pair sum includes the diagonal",
     12: "QUBO pairs read from the lower triangle",
+    13: "Potts pair term counts unequal states",
+    14: "Potts field table transposed",
 }
 
 
