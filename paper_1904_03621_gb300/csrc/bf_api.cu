@@ -121,9 +121,9 @@ bf_status make_plan(int n, int S, int dtype, const bf_options* opt, Plan& pl)
         int bps = bf::gray_blocks_per_sm(pl.list_cap);
         if (bps < 1) return fail(BF_ECUDA, "enumeration kernel does not fit on an SM (S=%d)", S);
         pl.grid = o.grid_blocks ? o.grid_blocks : sms * bps;
-        const int walk_bits = free_bits - bf::kInnerBits;    // middle + task-index bits
+        const int walk_bits = free_bits - bf::kGrayInnerBits;    // middle + task-index bits
         if (o.task_log2) {
-            pl.m = std::min(std::max(o.task_log2 - bf::kInnerBits, 0), walk_bits);
+            pl.m = std::min(std::max(o.task_log2 - bf::kGrayInnerBits, 0), walk_bits);
         } else {
             const int chains = ceil_log2((unsigned long long)pl.grid * bf::kGrayThreads * bf::kWalks);
             pl.m = std::min(std::max(walk_bits - (chains + 2), 0), 14);

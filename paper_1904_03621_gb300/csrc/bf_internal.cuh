@@ -21,8 +21,10 @@
 namespace bf {
 
 constexpr int kMaxN = 64;
-constexpr int kInnerBits = 9;                    // spins walked inside one unrolled block
-constexpr int kInnerSteps = 1 << kInnerBits;     // configurations per block and walk
+constexpr int kInnerBits = 9;                    // spins walked inside one unrolled block (batched walker)
+constexpr int kInnerSteps = 1 << kInnerBits;     // configurations per block and walk (batched walker)
+constexpr int kGrayInnerBits = 10;               // the same for the single-instance Gray walk
+constexpr int kGrayInnerSteps = 1 << kGrayInnerBits;
 constexpr int kKeep = 4;                         // middle spins whose local field is kept in registers
 constexpr int kWalks = 4;                        // walks (tasks) per thread: two packed words
 constexpr int kGrayThreads = 256;                // block size of the enumeration kernel
@@ -62,14 +64,14 @@ struct PrepLaunch {
     int tau0;             // seed threshold (INT32 max if none)
     double delta;         // quantisation residual bound (energy units)
     double emax;          // sum |J| + sum |h| (energy units)
-    unsigned dT16[kInnerSteps];   // packed 16-bit pair-energy increments of the inner walk
+    unsigned dT16[kGrayInnerSteps];   // packed 16-bit pair-energy increments of the inner walk
 };
 
 struct Prep {
     PrepLaunch L;
     int Jq[kMaxN * kMaxN];        // quantised symmetric couplings, zero diagonal
     int hq[kMaxN];
-    int T[kInnerSteps];           // exact inner pair energy T[g] (quantised units)
+    int T[kGrayInnerSteps];       // exact inner pair energy T[g] (quantised units)
     int colJ[kMaxN][16];          // column j: J_q[k][j] for the inner spins k, then the kept middle spins
 };
 
@@ -131,7 +133,7 @@ __host__ inline Layout make_layout(int S, int max_blocks, int spill_log2)
 // ---- kernel parameter blocks -------------------------------------------
 
 struct GrayParams {
-    unsigned dT16[kInnerSteps];     // index t = 1..kInnerSteps-1; entry 0 unused
+    unsigned dT16[kGrayInnerSteps]; // index t = 1..kGrayInnerSteps-1; entry 0 unused
     int n, m, nh;                   // spins, walked middle spins, task-index bits
     int free_bits;
     unsigned long long hiconst;     // fixed top bits of every configuration

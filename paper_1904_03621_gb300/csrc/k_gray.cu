@@ -9,13 +9,13 @@
 // dE = 2 s_new F_k (F_k the local field on the flipped spin k).
 //
 // Bit layout of a configuration c (bit i = spin i, 1 = +1):
-//   [0, 9)         inner spins: walked by a fully unrolled 511-step block
-//   [9, 9+m)       middle spins: walked one flip per block (dynamic index)
-//   [9+m, free)    task index (prefix) of the walk
+//   [0, 10)        inner spins: walked by a fully unrolled 1023-step block
+//   [10, 10+m)     middle spins: walked one flip per block (dynamic index)
+//   [10+m, free)   task index (prefix) of the walk
 //   [free, n)      fixed bits (subspace mode, Sec. 3, Eq. (6))
 //
 // Arithmetic: the quantised instance is exact in int32.  Per walk we keep
-// E0 (energy with all inner spins at -1), G_k = 2 F_k for the 9 inner spins
+// E0 (energy with all inner spins at -1), G_k = 2 F_k for the 10 inner spins
 // (fields from non-inner spins) and the local fields of 4 middle spins.
 // Inside a block, E(g) = E0 + sum_{k in g} G_k + T[g] - T[0].  The unrolled
 // walk runs on 16-bit values floor((E + 2^31) / 2^16), two walks packed per
@@ -23,7 +23,7 @@
 // minimum folds them into a running minimum.  A block whose 16-bit minimum
 // reaches the threshold is rescanned exactly in int32, and only exact hits
 // are recorded.  Error bound of the 16-bit value x(g) of a configuration:
-//   E(g)/2^16 - 11 < x(g) - 2^15 <= E(g)/2^16 + 1,
+//   E(g)/2^16 - 12 < x(g) - 2^15 <= E(g)/2^16 + 1,
 // so x(g) <= floor((tau + 2^31) / 2^16) + 1 catches every E(g) <= tau.
 //
 // Selection: hits go to a shared-memory buffer (spill area in the
@@ -45,7 +45,7 @@ __host__ __device__ constexpr bool cx_up(int t) { return (((t ^ (t >> 1)) >> cx_
 
 struct Packed {
     unsigned Xa, Xb, M;
-    unsigned Ga[kInnerBits], Gb[kInnerBits];
+    unsigned Ga[kGrayInnerBits], Gb[kGrayInnerBits];
 };
 
 template <int t>
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
     s.E = reinterpret_cast<int*>(s.C + 2 * cap);                            // 2*cap
     s.col = reinterpret_cast<int(*)[16]>(s.E + 2 * cap);                    // kMaxN*16
     s.T = reinterpret_cast<int*>(s.col + kMaxN);                            // 256
-    s.hq = s.T + kInnerSteps;                                               // kMaxN
+    s.hq = s.T + kGrayInnerSteps;                                               // kMaxN
     s.Jq = s.hq + kMaxN;                                                    // n*n
 
     __shared__ unsigned s_buf_count;
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
     const Prep* prep = p.prep;
     for (int i = tid; i < n * n; i += blockDim.x) s.Jq[i] = prep->Jq[i];
     for (int i = tid; i < kMaxN; i += blockDim.x) s.hq[i] = prep->hq[i];
-    for (int i = tid; i < kInnerSteps; i += blockDim.x) s.T[i] = prep->T[i];
+    for (int i = tid; i < kGrayInnerSteps; i += blockDim.x) s.T[i] = prep->T[i];
     for (int i = tid; i < kMaxN * 16; i += blockDim.x) s.col[i / 16][i % 16] = prep->colJ[i / 16][i % 16];
     if (tid == 0) {
         s_buf_count = 0u;
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
     __syncthreads();
 
     const int S = p.S, W = p.W, m = p.m;
-    const int walk_shift = kInnerBits + m;       // task index sits above inner + middle spins
+    const int walk_shift = kGrayInnerBits + m;       // task index sits above inner + middle spins
     const unsigned nblocks = 1u << m;
     const unsigned seg_mask = (1u << p.seg_log2) - 1u;
 
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
         if (base >= p.ntasks) break;
 
         // ---- per-walk state at the start of the task (middle and inner spins all -1)
-        int E0[kWalks], G[kWalks][kInnerBits], Fm[kWalks][kKeep];
+        int E0[kWalks], G[kWalks][kGrayInnerBits], Fm[kWalks][kKeep];
         unsigned long long cfg0[kWalks];
         bool active[kWalks];
 #pragma unroll
@@ -204,22 +204,22 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
             }
             E0[w] = e;
 #pragma unroll
-            for (int k = 0; k < kInnerBits; k++) {
+            for (int k = 0; k < kGrayInnerBits; k++) {
                 int f = s.hq[k];
                 const int* Jk = s.Jq + k * n;
-                for (int j = kInnerBits; j < n; j++) {
+                for (int j = kGrayInnerBits; j < n; j++) {
                     int v = Jk[j];
                     f += ((c >> j) & 1ull) ? v : -v;
                 }
                 G[w][k] = 2 * f;
             }
 #pragma unroll
-            for (int r = 0; r < kKeep; r++) Fm[w][r] = field_at(s, n, kInnerBits + r, c);
+            for (int r = 0; r < kKeep; r++) Fm[w][r] = field_at(s, n, kGrayInnerBits + r, c);
         }
 
         Packed pk;
 #pragma unroll
-        for (int k = 0; k < kInnerBits; k++) {
+        for (int k = 0; k < kGrayInnerBits; k++) {
             pk.Ga[k] = pack_hi16(G[0][k], G[1][k]);
             pk.Gb[k] = pack_hi16(G[2][k], G[3][k]);
         }
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
             pk.Xa = pack_energy(E0[0], E0[1]);
             pk.Xb = pack_energy(E0[2], E0[3]);
             pk.M = __vminu2(pk.Xa, pk.Xb);
-            inner_walk(pk, p, std::make_integer_sequence<int, kInnerSteps - 1>{});
+            inner_walk(pk, p, std::make_integer_sequence<int, kGrayInnerSteps - 1>{});
             const bool flag_lo = (pk.M & 0xffffu) <= thr16;
             const bool flag_hi = (pk.M >> 16) <= thr16;
             if (flag_lo || flag_hi) {
@@ -240,11 +240,11 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
                     if (!active[w] || !(lane_hi ? flag_hi : flag_lo)) continue;
                     const unsigned ebase = (unsigned)E0[w] - (unsigned)s.T[0];
                     const unsigned long long cb = cfg0[w] | cmid;
-                    for (int t = 0; t < kInnerSteps; t++) {
+                    for (int t = 0; t < kGrayInnerSteps; t++) {
                         const int g = t ^ (t >> 1);
                         unsigned acc = ebase + (unsigned)s.T[g];
 #pragma unroll
-                        for (int k = 0; k < kInnerBits; k++) acc += ((g >> k) & 1) ? (unsigned)G[w][k] : 0u;
+                        for (int k = 0; k < kGrayInnerBits; k++) acc += ((g >> k) & 1) ? (unsigned)G[w][k] : 0u;
                         const int e = (int)acc;   // E(g) = E0 + sum_{k in g} G_k + T[g] - T[0]
                         const unsigned long long c = cb | (unsigned long long)g;
                         if (e <= tau_scr && !(e == tie_E && c > tie_C)) record(p, s, &s_buf_count, e, c);
@@ -293,11 +293,11 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
                 refresh_threshold();
             }
 
-            // ---- flip one middle spin: j = kInnerBits + ctz(u + 1)
+            // ---- flip one middle spin: j = kGrayInnerBits + ctz(u + 1)
             if (u + 1 < nblocks) {
                 const unsigned u1 = u + 1;
                 const int jrel = __ffs(u1) - 1;
-                const int j = kInnerBits + jrel;
+                const int j = kGrayInnerBits + jrel;
                 const bool up = ((u1 ^ (u1 >> 1)) >> jrel) & 1u;
                 int F[kWalks];
                 if (jrel < kKeep) {
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
 #pragma unroll
                     for (int w = 0; w < kWalks; w++) F[w] = field_at(s, n, j, cfg0[w] | cmid);
                 }
-                static_assert(kInnerBits + kKeep <= 16, "column table holds 16 entries");
+                static_assert(kGrayInnerBits + kKeep <= 16, "column table holds 16 entries");
                 int colv[16];
 #pragma unroll
                 for (int q4 = 0; q4 < 4; q4++) {
@@ -328,19 +328,19 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
                     const unsigned dE = (unsigned)F[w] << 1;
                     E0[w] = (int)((unsigned)E0[w] + (up ? dE : 0u - dE));
 #pragma unroll
-                    for (int k = 0; k < kInnerBits; k++) {
+                    for (int k = 0; k < kGrayInnerBits; k++) {
                         const unsigned d = (unsigned)colv[k] << 2;
                         G[w][k] = (int)((unsigned)G[w][k] + (up ? d : 0u - d));
                     }
 #pragma unroll
                     for (int r = 0; r < kKeep; r++) {
-                        const unsigned d = (unsigned)colv[kInnerBits + r] << 1;
+                        const unsigned d = (unsigned)colv[kGrayInnerBits + r] << 1;
                         Fm[w][r] = (int)((unsigned)Fm[w][r] + (up ? d : 0u - d));
                     }
                 }
                 cmid ^= 1ull << j;
 #pragma unroll
-                for (int k = 0; k < kInnerBits; k++) {
+                for (int k = 0; k < kGrayInnerBits; k++) {
                     pk.Ga[k] = pack_hi16(G[0][k], G[1][k]);
                     pk.Gb[k] = pack_hi16(G[2][k], G[3][k]);
                 }
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
 
 size_t gray_smem_bytes(int n, int list_cap)
 {
-    return (size_t)2 * list_cap * 8 + (size_t)2 * list_cap * 4 + kMaxN * 16 * 4 + kInnerSteps * 4 + kMaxN * 4 +
+    return (size_t)2 * list_cap * 8 + (size_t)2 * list_cap * 4 + kMaxN * 16 * 4 + kGrayInnerSteps * 4 + kMaxN * 4 +
            (size_t)n * n * 4;
 }
 
