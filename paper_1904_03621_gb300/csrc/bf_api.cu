@@ -59,7 +59,7 @@ struct Plan {
     unsigned long long hiconst;
     bool direct;
     int variant;
-    int list_cap, grid, m, nh, seg_log2, seed_per_block, seed_blocks;
+    int list_cap, grid, m, nh, seg_log2, seed_per_block, seed_blocks, inner_bits;
     unsigned long long seed_sample;
     bf::Layout L;
     size_t bytes;
@@ -121,9 +121,10 @@ bf_status make_plan(int n, int S, int dtype, const bf_options* opt, Plan& pl)
         int bps = bf::gray_blocks_per_sm(pl.list_cap);
         if (bps < 1) return fail(BF_ECUDA, "enumeration kernel does not fit on an SM (S=%d)", S);
         pl.grid = o.grid_blocks ? o.grid_blocks : sms * bps;
-        const int walk_bits = free_bits - bf::kGrayInnerBits;    // middle + task-index bits
+        pl.inner_bits = bf::gray_inner_bits(free_bits);
+        const int walk_bits = free_bits - pl.inner_bits;           // middle + task-index bits
         if (o.task_log2) {
-            pl.m = std::min(std::max(o.task_log2 - bf::kGrayInnerBits, 0), walk_bits);
+            pl.m = std::min(std::max(o.task_log2 - pl.inner_bits, 0), walk_bits);
         } else {
             const int chains = ceil_log2((unsigned long long)pl.grid * bf::kGrayThreads * bf::kWalks);
             pl.m = std::min(std::max(walk_bits - (chains + 2), 0), 14);
@@ -233,6 +234,7 @@ bf_status bf_low_spectrum(const void* J, const void* h, int n, int S, bf_dtype d
     pp.hiconst = pl.hiconst;
     // the tensor-core variant needs 4x headroom: its cross coefficients reach 4 sum|J|
     pp.emq_log2 = pl.variant == BF_VARIANT_TC ? bf::kEmqLog2 - 2 : bf::kEmqLog2;
+    pp.inner_bits = pl.variant == BF_VARIANT_TC ? 9 : pl.inner_bits;
     pp.prep = prep;
     pp.hdr = hdr;
     cudaError_t e = bf::launch_prep(pp, stream);
@@ -274,6 +276,7 @@ bf_status bf_low_spectrum(const void* J, const void* h, int n, int S, bf_dtype d
     gp.list_cap = L.list_cap;
     gp.W = hl.W;
     gp.seg_log2 = pl.seg_log2;
+    gp.inner_bits = pl.inner_bits;
     gp.spill_cap = L.spill_cap;
     gp.prep = prep;
     gp.hdr = hdr;

@@ -23,8 +23,14 @@ namespace bf {
 constexpr int kMaxN = 64;
 constexpr int kInnerBits = 9;                    // spins walked inside one unrolled block (batched walker)
 constexpr int kInnerSteps = 1 << kInnerBits;     // configurations per block and walk (batched walker)
-constexpr int kGrayInnerBits = 10;               // the same for the single-instance Gray walk
-constexpr int kGrayInnerSteps = 1 << kGrayInnerBits;
+constexpr int kGrayMaxInnerBits = 10;            // the same for the single-instance Gray walk (9 or 10)
+constexpr int kGrayMaxInnerSteps = 1 << kGrayMaxInnerBits;
+constexpr int kGrayLargeFreeBits = 42;           // searches of >= 2^42 configurations use 10 inner spins
+
+// inner spins of the Gray walk for a search over 2^free_bits configurations: the larger
+// block amortises the once-per-block middle flip, the smaller one halves the exact rescans
+// of flagged blocks, which dominate short searches
+__host__ __device__ constexpr int gray_inner_bits(int free_bits) { return free_bits >= kGrayLargeFreeBits ? 10 : 9; }
 constexpr int kKeep = 4;                         // middle spins whose local field is kept in registers
 constexpr int kWalks = 4;                        // walks (tasks) per thread: two packed words
 constexpr int kGrayThreads = 256;                // block size of the enumeration kernel
@@ -64,14 +70,14 @@ struct PrepLaunch {
     int tau0;             // seed threshold (INT32 max if none)
     double delta;         // quantisation residual bound (energy units)
     double emax;          // sum |J| + sum |h| (energy units)
-    unsigned dT16[kGrayInnerSteps];   // packed 16-bit pair-energy increments of the inner walk
+    unsigned dT16[kGrayMaxInnerSteps];   // packed 16-bit pair-energy increments of the inner walk
 };
 
 struct Prep {
     PrepLaunch L;
     int Jq[kMaxN * kMaxN];        // quantised symmetric couplings, zero diagonal
     int hq[kMaxN];
-    int T[kGrayInnerSteps];       // exact inner pair energy T[g] (quantised units)
+    int T[kGrayMaxInnerSteps];    // exact inner pair energy T[g] (quantised units)
     int colJ[kMaxN][16];          // column j: J_q[k][j] for the inner spins k, then the kept middle spins
 };
 
@@ -133,14 +139,14 @@ __host__ inline Layout make_layout(int S, int max_blocks, int spill_log2)
 // ---- kernel parameter blocks -------------------------------------------
 
 struct GrayParams {
-    unsigned dT16[kGrayInnerSteps]; // index t = 1..kGrayInnerSteps-1; entry 0 unused
+    unsigned dT16[kGrayMaxInnerSteps]; // index t = 1..2^inner_bits - 1; entry 0 unused
     int n, m, nh;                   // spins, walked middle spins, task-index bits
     int free_bits;
     unsigned long long hiconst;     // fixed top bits of every configuration
     unsigned long long ntasks;      // 2^nh
     int S, list_cap, W, seg_log2;
     unsigned spill_cap;
-    int pad0;
+    int inner_bits;                 // spins of the unrolled block (9 or 10)
     const Prep* prep;
     WsHeader* hdr;
     int* list_E;
@@ -155,7 +161,7 @@ struct PrepParams {
     int n, dtype, S, free_bits;
     unsigned long long hiconst;
     int emq_log2;                   // |E_q| and |local fields| < 2^emq_log2
-    int pad0;
+    int inner_bits;                 // inner spins of the Gray walk the tables are built for
     Prep* prep;
     WsHeader* hdr;
 };

@@ -9,13 +9,14 @@
 // dE = 2 s_new F_k (F_k the local field on the flipped spin k).
 //
 // Bit layout of a configuration c (bit i = spin i, 1 = +1):
-//   [0, 10)        inner spins: walked by a fully unrolled 1023-step block
-//   [10, 10+m)     middle spins: walked one flip per block (dynamic index)
-//   [10+m, free)   task index (prefix) of the walk
+//   [0, B)         inner spins: walked by a fully unrolled (2^B - 1)-step block,
+//                  B = 10 for searches of >= 2^42 configurations, else 9
+//   [B, B+m)       middle spins: walked one flip per block (dynamic index)
+//   [B+m, free)    task index (prefix) of the walk
 //   [free, n)      fixed bits (subspace mode, Sec. 3, Eq. (6))
 //
 // Arithmetic: the quantised instance is exact in int32.  Per walk we keep
-// E0 (energy with all inner spins at -1), G_k = 2 F_k for the 10 inner spins
+// E0 (energy with all inner spins at -1), G_k = 2 F_k for the B inner spins
 // (fields from non-inner spins) and the local fields of 4 middle spins.
 // Inside a block, E(g) = E0 + sum_{k in g} G_k + T[g] - T[0].  The unrolled
 // walk runs on 16-bit values floor((E + 2^31) / 2^16), two walks packed per
@@ -23,7 +24,7 @@
 // minimum folds them into a running minimum.  A block whose 16-bit minimum
 // reaches the threshold is rescanned exactly in int32, and only exact hits
 // are recorded.  Error bound of the 16-bit value x(g) of a configuration:
-//   E(g)/2^16 - 12 < x(g) - 2^15 <= E(g)/2^16 + 1,
+//   E(g)/2^16 - (B + 2) < x(g) - 2^15 <= E(g)/2^16 + 1,
 // so x(g) <= floor((tau + 2^31) / 2^16) + 1 catches every E(g) <= tau.
 //
 // Selection: hits go to a shared-memory buffer (spill area in the
@@ -43,13 +44,14 @@ __host__ __device__ constexpr int cx_ctz(int t) { return (t & 1) ? 0 : 1 + cx_ct
 // value (1 = +1) of the spin flipped by step t of the reflected Gray code
 __host__ __device__ constexpr bool cx_up(int t) { return (((t ^ (t >> 1)) >> cx_ctz(t)) & 1) != 0; }
 
+template <int IB>
 struct Packed {
     unsigned Xa, Xb, M;
-    unsigned Ga[kGrayInnerBits], Gb[kGrayInnerBits];
+    unsigned Ga[IB], Gb[IB];
 };
 
-template <int t>
-__device__ __forceinline__ void inner_step(Packed& w, const GrayParams& p)
+template <int IB, int t>
+__device__ __forceinline__ void inner_step(Packed<IB>& w, const GrayParams& p)
 {
     constexpr int k = cx_ctz(t);
     constexpr bool up = cx_up(t);
@@ -58,10 +60,10 @@ __device__ __forceinline__ void inner_step(Packed& w, const GrayParams& p)
     w.M = __vminu2(__vminu2(w.M, w.Xa), w.Xb);
 }
 
-template <int... Ts>
-__device__ __forceinline__ void inner_walk(Packed& w, const GrayParams& p, std::integer_sequence<int, Ts...>)
+template <int IB, int... Ts>
+__device__ __forceinline__ void inner_walk(Packed<IB>& w, const GrayParams& p, std::integer_sequence<int, Ts...>)
 {
-    (inner_step<Ts + 1>(w, p), ...);
+    (inner_step<IB, Ts + 1>(w, p), ...);
 }
 
 // integer packing hi * 2^16 + lo of the 16-bit views (floor(x / 2^16)) of two int32 values
@@ -116,8 +118,10 @@ __device__ __forceinline__ int field_at(const Smem& s, int n, int j, unsigned lo
 
 }  // namespace
 
+template <int IB>
 __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_constant__ GrayParams p)
 {
+    constexpr int IS = 1 << IB;                  // configurations per unrolled block and walk
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = p.n;
     const int cap = p.list_cap;
@@ -126,7 +130,7 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
     s.E = reinterpret_cast<int*>(s.C + 2 * cap);                            // 2*cap
     s.col = reinterpret_cast<int(*)[16]>(s.E + 2 * cap);                    // kMaxN*16
     s.T = reinterpret_cast<int*>(s.col + kMaxN);                            // 256
-    s.hq = s.T + kGrayInnerSteps;                                               // kMaxN
+    s.hq = s.T + kGrayMaxInnerSteps;                                               // kMaxN
     s.Jq = s.hq + kMaxN;                                                    // n*n
 
     __shared__ unsigned s_buf_count;
@@ -137,7 +141,7 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
     const Prep* prep = p.prep;
     for (int i = tid; i < n * n; i += blockDim.x) s.Jq[i] = prep->Jq[i];
     for (int i = tid; i < kMaxN; i += blockDim.x) s.hq[i] = prep->hq[i];
-    for (int i = tid; i < kGrayInnerSteps; i += blockDim.x) s.T[i] = prep->T[i];
+    for (int i = tid; i < IS; i += blockDim.x) s.T[i] = prep->T[i];
     for (int i = tid; i < kMaxN * 16; i += blockDim.x) s.col[i / 16][i % 16] = prep->colJ[i / 16][i % 16];
     if (tid == 0) {
         s_buf_count = 0u;
@@ -148,7 +152,7 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
     __syncthreads();
 
     const int S = p.S, W = p.W, m = p.m;
-    const int walk_shift = kGrayInnerBits + m;       // task index sits above inner + middle spins
+    const int walk_shift = IB + m;       // task index sits above inner + middle spins
     const unsigned nblocks = 1u << m;
     const unsigned seg_mask = (1u << p.seg_log2) - 1u;
 
@@ -179,7 +183,7 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
         if (base >= p.ntasks) break;
 
         // ---- per-walk state at the start of the task (middle and inner spins all -1)
-        int E0[kWalks], G[kWalks][kGrayInnerBits], Fm[kWalks][kKeep];
+        int E0[kWalks], G[kWalks][IB], Fm[kWalks][kKeep];
         unsigned long long cfg0[kWalks];
         bool active[kWalks];
 #pragma unroll
@@ -204,22 +208,22 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
             }
             E0[w] = e;
 #pragma unroll
-            for (int k = 0; k < kGrayInnerBits; k++) {
+            for (int k = 0; k < IB; k++) {
                 int f = s.hq[k];
                 const int* Jk = s.Jq + k * n;
-                for (int j = kGrayInnerBits; j < n; j++) {
+                for (int j = IB; j < n; j++) {
                     int v = Jk[j];
                     f += ((c >> j) & 1ull) ? v : -v;
                 }
                 G[w][k] = 2 * f;
             }
 #pragma unroll
-            for (int r = 0; r < kKeep; r++) Fm[w][r] = field_at(s, n, kGrayInnerBits + r, c);
+            for (int r = 0; r < kKeep; r++) Fm[w][r] = field_at(s, n, IB + r, c);
         }
 
-        Packed pk;
+        Packed<IB> pk;
 #pragma unroll
-        for (int k = 0; k < kGrayInnerBits; k++) {
+        for (int k = 0; k < IB; k++) {
             pk.Ga[k] = pack_hi16(G[0][k], G[1][k]);
             pk.Gb[k] = pack_hi16(G[2][k], G[3][k]);
         }
@@ -230,7 +234,7 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
             pk.Xa = pack_energy(E0[0], E0[1]);
             pk.Xb = pack_energy(E0[2], E0[3]);
             pk.M = __vminu2(pk.Xa, pk.Xb);
-            inner_walk(pk, p, std::make_integer_sequence<int, kGrayInnerSteps - 1>{});
+            inner_walk<IB>(pk, p, std::make_integer_sequence<int, IS - 1>{});
             const bool flag_lo = (pk.M & 0xffffu) <= thr16;
             const bool flag_hi = (pk.M >> 16) <= thr16;
             if (flag_lo || flag_hi) {
@@ -240,11 +244,11 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
                     if (!active[w] || !(lane_hi ? flag_hi : flag_lo)) continue;
                     const unsigned ebase = (unsigned)E0[w] - (unsigned)s.T[0];
                     const unsigned long long cb = cfg0[w] | cmid;
-                    for (int t = 0; t < kGrayInnerSteps; t++) {
+                    for (int t = 0; t < IS; t++) {
                         const int g = t ^ (t >> 1);
                         unsigned acc = ebase + (unsigned)s.T[g];
 #pragma unroll
-                        for (int k = 0; k < kGrayInnerBits; k++) acc += ((g >> k) & 1) ? (unsigned)G[w][k] : 0u;
+                        for (int k = 0; k < IB; k++) acc += ((g >> k) & 1) ? (unsigned)G[w][k] : 0u;
                         const int e = (int)acc;   // E(g) = E0 + sum_{k in g} G_k + T[g] - T[0]
                         const unsigned long long c = cb | (unsigned long long)g;
                         if (e <= tau_scr && !(e == tie_E && c > tie_C)) record(p, s, &s_buf_count, e, c);
@@ -293,11 +297,11 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
                 refresh_threshold();
             }
 
-            // ---- flip one middle spin: j = kGrayInnerBits + ctz(u + 1)
+            // ---- flip one middle spin: j = IB + ctz(u + 1)
             if (u + 1 < nblocks) {
                 const unsigned u1 = u + 1;
                 const int jrel = __ffs(u1) - 1;
-                const int j = kGrayInnerBits + jrel;
+                const int j = IB + jrel;
                 const bool up = ((u1 ^ (u1 >> 1)) >> jrel) & 1u;
                 int F[kWalks];
                 if (jrel < kKeep) {
@@ -312,7 +316,7 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
 #pragma unroll
                     for (int w = 0; w < kWalks; w++) F[w] = field_at(s, n, j, cfg0[w] | cmid);
                 }
-                static_assert(kGrayInnerBits + kKeep <= 16, "column table holds 16 entries");
+                static_assert(IB + kKeep <= 16, "column table holds 16 entries");
                 int colv[16];
 #pragma unroll
                 for (int q4 = 0; q4 < 4; q4++) {
@@ -328,19 +332,19 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
                     const unsigned dE = (unsigned)F[w] << 1;
                     E0[w] = (int)((unsigned)E0[w] + (up ? dE : 0u - dE));
 #pragma unroll
-                    for (int k = 0; k < kGrayInnerBits; k++) {
+                    for (int k = 0; k < IB; k++) {
                         const unsigned d = (unsigned)colv[k] << 2;
                         G[w][k] = (int)((unsigned)G[w][k] + (up ? d : 0u - d));
                     }
 #pragma unroll
                     for (int r = 0; r < kKeep; r++) {
-                        const unsigned d = (unsigned)colv[kGrayInnerBits + r] << 1;
+                        const unsigned d = (unsigned)colv[IB + r] << 1;
                         Fm[w][r] = (int)((unsigned)Fm[w][r] + (up ? d : 0u - d));
                     }
                 }
                 cmid ^= 1ull << j;
 #pragma unroll
-                for (int k = 0; k < kGrayInnerBits; k++) {
+                for (int k = 0; k < IB; k++) {
                     pk.Ga[k] = pack_hi16(G[0][k], G[1][k]);
                     pk.Gb[k] = pack_hi16(G[2][k], G[3][k]);
                 }
@@ -358,30 +362,37 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
 
 size_t gray_smem_bytes(int n, int list_cap)
 {
-    return (size_t)2 * list_cap * 8 + (size_t)2 * list_cap * 4 + kMaxN * 16 * 4 + kGrayInnerSteps * 4 + kMaxN * 4 +
-           (size_t)n * n * 4;
+    return (size_t)2 * list_cap * 8 + (size_t)2 * list_cap * 4 + kMaxN * 16 * 4 + kGrayMaxInnerSteps * 4 +
+           kMaxN * 4 + (size_t)n * n * 4;
 }
 
+// both block sizes use the same shared memory and at most 128 registers (2 blocks per SM)
 int gray_blocks_per_sm(int list_cap)
 {
     int blocks = 0;
     size_t smem = gray_smem_bytes(kMaxN, list_cap);
-    if (cudaFuncSetAttribute(gray_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(gray_kernel<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, gray_kernel, kGrayThreads, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, gray_kernel<10>, kGrayThreads, smem) != cudaSuccess)
         return 0;
     return blocks;
 }
 
-cudaError_t launch_gray(const GrayParams& p, int grid, cudaStream_t s)
+template <int IB>
+cudaError_t launch_gray_ib(const GrayParams& p, int grid, cudaStream_t s)
 {
     size_t smem = gray_smem_bytes(p.n, p.list_cap);
-    cudaError_t e = cudaFuncSetAttribute(gray_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(gray_kernel<IB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)gray_smem_bytes(kMaxN, p.list_cap));
     if (e != cudaSuccess) return e;
-    gray_kernel<<<grid, kGrayThreads, smem, s>>>(p);
+    gray_kernel<IB><<<grid, kGrayThreads, smem, s>>>(p);
     count_launches(1);
     return cudaGetLastError();
+}
+
+cudaError_t launch_gray(const GrayParams& p, int grid, cudaStream_t s)
+{
+    return p.inner_bits == 10 ? launch_gray_ib<10>(p, grid, s) : launch_gray_ib<9>(p, grid, s);
 }
 
 }  // namespace bf

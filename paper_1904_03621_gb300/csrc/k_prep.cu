@@ -124,13 +124,14 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(const PrepParams p)
     if (tid == 0) s_delta = delta;
     __syncthreads();
 
-    // 6. inner pair energies T[g] = sum_{i<k} J_q,ik s_i s_k over the kGrayInnerBits spins walked inside a block
-    for (int g = tid; g < kGrayInnerSteps; g += blockDim.x) {
+    // 6. inner pair energies T[g] = sum_{i<k} J_q,ik s_i s_k over the IB spins walked inside a block
+    const int IB = p.inner_bits, IS = 1 << IB;
+    for (int g = tid; g < kGrayMaxInnerSteps; g += blockDim.x) {
         int t = 0;
-        if (n >= kGrayInnerBits) {
-            for (int i = 0; i < kGrayInnerBits; i++) {
+        if (n >= IB && g < IS) {
+            for (int i = 0; i < IB; i++) {
                 int si = ((g >> i) & 1) ? 1 : -1;
-                for (int k = i + 1; k < kGrayInnerBits; k++) {
+                for (int k = i + 1; k < IB; k++) {
                     int sk = ((g >> k) & 1) ? 1 : -1;
                     t += Jq[i * n + k] * si * sk;
                 }
@@ -143,15 +144,15 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(const PrepParams p)
     // 8. outputs
     for (int idx = tid; idx < n * n; idx += blockDim.x) out->Jq[idx] = Jq[idx];
     for (int i = tid; i < kMaxN; i += blockDim.x) out->hq[i] = (i < n) ? hq[i] : 0;
-    for (int g = tid; g < kGrayInnerSteps; g += blockDim.x) out->T[g] = Tq[g];
+    for (int g = tid; g < kGrayMaxInnerSteps; g += blockDim.x) out->T[g] = Tq[g];
     for (int idx = tid; idx < kMaxN * 16; idx += blockDim.x) {
         int j = idx / 16, k = idx % 16;
-        int row = (k < kGrayInnerBits) ? k : (k < kGrayInnerBits + kKeep ? k : -1);
+        int row = (k < IB) ? k : (k < IB + kKeep ? k : -1);
         out->colJ[j][k] = (j < n && row >= 0 && row < n) ? Jq[row * n + j] : 0;
     }
-    for (int t = tid; t < kGrayInnerSteps; t += blockDim.x) {
+    for (int t = tid; t < kGrayMaxInnerSteps; t += blockDim.x) {
         unsigned v = 0;
-        if (t > 0) {
+        if (t > 0 && t < IS) {
             int g1 = t ^ (t >> 1), g0 = (t - 1) ^ ((t - 1) >> 1);
             int d = (Tq[g1] >> 16) - (Tq[g0] >> 16);     // floor(T / 2^16) differences
             v = (unsigned)d * 65537u;                     // same increment in both 16-bit lanes
@@ -286,7 +287,7 @@ __global__ void __launch_bounds__(kDirectThreads) direct_kernel(const void* J, c
 cudaError_t launch_prep(const PrepParams& p, cudaStream_t s)
 {
     size_t smem = (size_t)p.n * p.n * 8 + kMaxN * 8 + kPrepThreads * 8 + kMaxN * kMaxN * 4 + kMaxN * 4 +
-                  kGrayInnerSteps * 4;
+                  kGrayMaxInnerSteps * 4;
     cudaError_t e = cudaFuncSetAttribute(prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     prep_kernel<<<1, kPrepThreads, smem, s>>>(p);

@@ -121,7 +121,7 @@ def test_batched_invalid_n(bf):
 
 def test_batched_4096_sample(bf):
     """The 4096-instance workload (2048 dense, 2048 Chimera, n in [16, 28], S = 10) in one
-    call; 96 sampled instances against stored oracle results."""
+    call; 96 sampled instances against stored oracle results, all instances by properties."""
     import importlib.util
     path = os.path.join(GOLDEN, "batched_sample_S10.txt.gz")
     if not os.path.exists(path):
@@ -142,6 +142,27 @@ def test_batched_4096_sample(bf):
             assert_int_equal(en[i], st[i], en_o, st_o)
         else:
             assert_float_parity(o, J, h, en[i], st[i], en_o, st_o)
+    # every instance, by properties that hold at any size: returned energies are the oracle's
+    # energies of the returned states, ascending by (E, c), no duplicates; and on 256 sampled
+    # instances, every single-spin-flip neighbour below the S-th energy is returned
+    from parity import tolerance
+    rng = np.random.default_rng(11)
+    closure = set(rng.choice(len(insts), 256, replace=False).tolist())
+    for i, (J, h, kind) in enumerate(insts):
+        n = J.shape[0]
+        tol = 0.0 if kind == "sparse" else tolerance(J, h)
+        e_i, s_i = en[i], st[i]
+        assert len(set(s_i.tolist())) == len(s_i), i
+        assert np.all(np.diff(e_i) >= 0), i
+        for k in range(len(s_i)):
+            assert abs(o.energy(J, h, int(s_i[k])) - e_i[k]) <= tol, (i, k)
+        if i in closure:
+            members = set(int(c) for c in s_i)
+            for c in s_i:
+                for b in range(n):
+                    nb = int(c) ^ (1 << b)
+                    if o.energy(J, h, nb) < e_i[-1] - tol:
+                        assert nb in members, (i, int(c), b)
 
 
 def test_batched_autotune(bf, o):

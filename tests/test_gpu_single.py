@@ -227,3 +227,39 @@ def test_float_n48_subspaces(bf, o):
         en, st = run(bf, J, h, mg.N48_S, fixed_bits=mg.N48_FIXED_BITS, fixed_value=v)
         # stored records have S entries: parity without the (S+1)-th gap check
         assert_float_parity(o, J, h, en, st, en_o, st_o)
+
+
+def test_float_n48_full_search_properties(bf, o):
+    """The benchmark workload itself: all 2^48 configurations of the n = 48 float instance,
+    S = 1000, in the launch configuration bench.py times (default options).  The oracle
+    cannot enumerate 2^48, so the result is checked by properties that hold at any size:
+      - every returned energy equals the oracle's FP64 energy of that state (tolerance of
+        parity.tolerance), the list ascends by (E, c) and has no duplicates;
+      - closure: a single-spin-flip neighbour of a returned state with lower energy is
+        itself returned (it lies below the S-th energy), 48 000 oracle evaluations;
+      - rank by rank, the energies lie at or below the lowest records of the union of the
+        64 stored oracle subspace lists (a subset of the space cannot beat the whole).
+    """
+    from parity import tolerance
+    J, h = instances.float_n48()
+    S = 1000
+    en, st = run(bf, J, h, S)
+    tol = tolerance(J, h)
+    assert len(set(st.tolist())) == S
+    for k in range(S):
+        assert abs(o.energy(J, h, int(st[k])) - en[k]) <= tol, k
+    d = np.diff(en)
+    assert np.all(d >= 0), "energies not ascending"
+    assert np.all(np.diff(st.astype(np.float64))[d == 0] > 0), "equal energies not ordered by c"
+    members = set(int(c) for c in st)
+    e_cut = en[-1]
+    for k in range(S):
+        c = int(st[k])
+        for i in range(48):
+            nb = c ^ (1 << i)
+            e_nb = o.energy(J, h, nb)
+            if e_nb < e_cut - tol:
+                assert nb in members, f"neighbour {nb} of rank {k} (E={e_nb}) below the cut {e_cut} is missing"
+    mg, gold = _golden("float_n48_sub24_S1000.txt.gz")
+    union = np.sort(np.concatenate([np.asarray(v[0], dtype=np.float64) for v in gold.values()]))[:S]
+    assert np.all(en <= union + tol)
