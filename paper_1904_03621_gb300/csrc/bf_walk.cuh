@@ -1,7 +1,7 @@
 // Primitives of the Gray-code walk shared by the enumeration kernels.
 //
-// Reflected Gray code over the 8 inner spins: step t (1..255) flips spin
-// ctz(t) to the value of that bit in gray(t) = t ^ (t >> 1).  The 16-bit
+// Reflected Gray code over the kInnerBits inner spins: step t (1 .. 2^kInnerBits - 1)
+// flips spin ctz(t) to the value of that bit in gray(t) = t ^ (t >> 1).  The 16-bit
 // view of an int32 energy or field is floor(x / 2^16); two walks share one
 // 32-bit register as the integer hi * 2^16 + lo, so one 32-bit add advances
 // both exactly while every lane stays inside [0, 2^16).

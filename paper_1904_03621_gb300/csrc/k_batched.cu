@@ -63,9 +63,63 @@ __device__ double block_sum(double v, double* red)
     return r;
 }
 
+// Seed walks over the 9 inner spins in chunks of 32 Gray steps t = 32 j + i.  For
+// 1 <= i <= 31 the flipped spin is k = ctz(i) <= 4 and its new value is bit k of
+// gray(t) = 1 ^ bit (k+1) of t: known at compile time for k < 4, the parity of j for k = 4.
+// The step entering chunk j >= 1 flips spin 5 + ctz(j).
+static_assert(kInnerBits == 9, "seed walk chunking assumes 9 inner spins");
+
+template <int i>
+__device__ __forceinline__ void seed_step(int& e, int& best, const int (&G)[kInnerBits], const int (&d)[32], bool odd)
+{
+    constexpr int k = cx_ctz(i);
+    int g;
+    if constexpr (k < 4) {
+        constexpr bool up = ((i >> (k + 1)) & 1) == 0;
+        g = up ? G[k] : -G[k];
+    } else {
+        g = odd ? -G[4] : G[4];
+    }
+    e = (int)((unsigned)e + (unsigned)g + (unsigned)d[i]);
+    best = min(best, e);
+}
+
+template <int... Is>
+__device__ __forceinline__ void seed_chunk(int& e, int& best, const int (&G)[kInnerBits], const int (&d)[32], bool odd,
+                                           std::integer_sequence<int, Is...>)
+{
+    (seed_step<Is + 1>(e, best, G, d, odd), ...);
+}
+
+// minimum of the exact energies of the 2^9 configurations of one seed walk (e: energy at g = 0)
+__device__ __forceinline__ void seed_walk(int e, int& best, const int (&G)[kInnerBits], const int* dTx)
+{
+#pragma unroll 1
+    for (int j = 0; j < kInnerSteps / 32; j++) {
+        int d[32];
+        const int4* d4 = reinterpret_cast<const int4*>(dTx + 32 * j);
+#pragma unroll
+        for (int v = 0; v < 8; v++) {
+            const int4 x = d4[v];
+            d[4 * v] = x.x;
+            d[4 * v + 1] = x.y;
+            d[4 * v + 2] = x.z;
+            d[4 * v + 3] = x.w;
+        }
+        if (j > 0) {
+            const int cj = __ffs(j) - 1;                  // spin 5 + cj flips
+            const bool up = ((j >> (cj + 1)) & 1) == 0;
+            const int gk = cj == 0 ? G[5] : cj == 1 ? G[6] : cj == 2 ? G[7] : G[8];
+            e = (int)((unsigned)e + (up ? (unsigned)gk : 0u - (unsigned)gk) + (unsigned)d[0]);
+            best = min(best, e);
+        }
+        seed_chunk(e, best, G, d, (j & 1) != 0, std::make_integer_sequence<int, 31>{});
+    }
+}
+
 // ---- per-instance preparation: one block per instance -----------------------
 
-__global__ void __launch_bounds__(kBSeedThreads) bprep_kernel(const BatchParams p)
+__global__ void __launch_bounds__(kBSeedThreads, 2) bprep_kernel(const BatchParams p)
 {
     __shared__ double Jd[kBMaxN * kBMaxN];
     __shared__ double hd[kBMaxN];
@@ -73,6 +127,7 @@ __global__ void __launch_bounds__(kBSeedThreads) bprep_kernel(const BatchParams 
     __shared__ int Jq[kBMaxN * kBMaxN];
     __shared__ int hq[kBMaxN];
     __shared__ int Tq[kInnerSteps];
+    __shared__ __align__(16) int dTx[kInnerSteps];   // exact T[gray(t)] - T[gray(t-1)]
     __shared__ int sE[kBSeed];
     __shared__ unsigned long long sC[kBSeed];
     __shared__ int s_q, s_status;
@@ -151,9 +206,17 @@ __global__ void __launch_bounds__(kBSeedThreads) bprep_kernel(const BatchParams 
         Tq[g] = t;
     }
     __syncthreads();
-    // first threshold.  n >= 18: each of the 256 threads Gray-walks its own 2^10 configurations
-    // (low 10 spins free, the rest fixed to a distinct pattern) and keeps the lowest; the
-    // S-th lowest of those 256 minima bounds the S-th energy of the instance from above.
+    for (int s = tid; s < kInnerSteps; s += blockDim.x) {
+        const int g1 = s ^ (s >> 1), g0 = (s - 1) ^ ((s - 1) >> 1);
+        dTx[s] = s > 0 ? Tq[g1] - Tq[g0] : 0;
+    }
+    __syncthreads();
+    // first threshold.  n >= 18: each of the 256 threads walks its own 2^10 configurations
+    // (low 10 spins free, the rest fixed to a distinct pattern) and keeps the lowest energy;
+    // the S-th lowest of those 256 minima (energies of distinct configurations) bounds the
+    // S-th energy of the instance from above.  The walk is the main walker's
+    // decomposition E(g) = E0 + sum_{k in g} G_k + T[g] - T[0] over the 9 inner spins, twice
+    // (spin 9 at -1, then at +1), one add per configuration.
     // Smaller n: exact energies of a pseudo-random sample of 1024 (all if fewer).
     const unsigned long long space = 1ull << n;
     if (n >= 18) {
@@ -168,27 +231,25 @@ __global__ void __launch_bounds__(kBSeedThreads) bprep_kernel(const BatchParams 
             for (int j = i + 1; j < n; j++) row += ((c >> j) & 1ull) ? Jq[i * n + j] : -Jq[i * n + j];
             e += ((c >> i) & 1ull) ? row : -row;
         }
-        int f[10];
-        for (int k = 0; k < 10; k++) {          // local fields of the walked spins (all -1 now)
+        // G_k = 2 (h_k + sum_{j >= 9} J_kj s_j), F9 = field of spin 9 (inner spins at -1)
+        int G[kInnerBits];
+#pragma unroll
+        for (int k = 0; k < kInnerBits; k++) {
             int v = hq[k];
-            for (int j = 0; j < n; j++) v += ((c >> j) & 1ull) ? Jq[k * n + j] : -Jq[k * n + j];
-            f[k] = v;
+            for (int j = kInnerBits; j < n; j++) v += ((c >> j) & 1ull) ? Jq[k * n + j] : -Jq[k * n + j];
+            G[k] = 2 * v;
         }
+        int f9 = hq[kInnerBits];
+        for (int j = 0; j < n; j++) f9 += ((c >> j) & 1ull) ? Jq[kInnerBits * n + j] : -Jq[kInnerBits * n + j];
         int best = e;
-        unsigned long long bestc = c;
-        for (int t = 1; t < 1024; t++) {
-            const int k = __ffs(t) - 1;
-            const bool up = (((t ^ (t >> 1)) >> k) & 1) != 0;
-            int fk = 0;
-            for (int r = 0; r < 10; r++) fk = (r == k) ? f[r] : fk;
-            e += up ? 2 * fk : -2 * fk;
-            c ^= 1ull << k;
-            for (int r = 0; r < 10; r++) {
-                const int d = 2 * Jq[r * n + k];
-                f[r] += (r == k) ? 0 : (up ? d : -d);
-            }
-            if (e < best) { best = e; bestc = c; }
-        }
+        seed_walk(e, best, G, dTx);
+        // spin 9 from -1 to +1 (inner spins at -1): E += 2 F9, G_k += 4 J_k9
+        const int e1 = (int)((unsigned)e + ((unsigned)f9 << 1));
+        best = min(best, e1);
+#pragma unroll
+        for (int k = 0; k < kInnerBits; k++) G[k] = (int)((unsigned)G[k] + ((unsigned)Jq[k * n + kInnerBits] << 2));
+        seed_walk(e1, best, G, dTx);
+        const unsigned long long bestc = c;     // distinct per thread: orders equal minima
         sE[tid] = best;
         sC[tid] = bestc;
     } else {
