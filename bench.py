@@ -350,6 +350,19 @@ def potts_bench(args):
     configs = float(q) ** n
     t = float(np.median(times))
     tk = float(np.median(kern))
+    # the oracle's Potts enumeration on this host, on a smaller instance of the same recipe
+    import oracle
+    o = oracle.get()
+    n_cpu = n
+    while float(q) ** n_cpu > 2 ** 22:
+        n_cpu -= 1
+    Jc, hc = J[:n_cpu, :n_cpu], h[:n_cpu]
+    t0 = time.perf_counter()
+    o.potts_low_spectrum(Jc, hc, S)
+    dt_cpu = time.perf_counter() - t0
+    cpu = {"value": float(q) ** n_cpu / dt_cpu, "unit": "configs/s", "cores": o.num_threads, "kind": "oracle",
+           "sample": f"all {q}^{n_cpu} configurations of the leading {n_cpu}-spin block of the instance, S={S}, "
+                     f"{dt_cpu:.1f} s"}
     pk = peaks()
     mhz = clocks.get("sm_max_mhz") or 2070.0
     peak = 152 * 64 * mhz * 1e6 / 1e9
@@ -360,9 +373,122 @@ def potts_bench(args):
             "config": {"workload": f"potts_q{q}_n{n}", "q": q, "n": n, "S": S, "configs_per_step": configs},
             "roofline": {"bound": "alu", "kernel": "potts_walk_kernel", "achieved": achieved, "peak": peak,
                          "unit": "Gop/s", "frac": achieved / peak, "ops_per_config": 1.5, "kernel_ms": tk * 1e3},
-            "clocks": clocks}
+            "clocks": clocks, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def batched_only(args):
+    """The batched workload alone: 4096 instances (2048 dense n ~ U{16..28}, 2048 Chimera), S = 10,
+    W untimed and K timed calls of the public batched search on inputs resident in HBM, CUDA
+    events around each call.  One JSON line."""
+    import torch
+    from paper_1904_03621_gb300 import build, instances
+    build.build()
+    from paper_1904_03621_gb300 import api
+    insts = instances.batched_4096()
+    packed = api.pack_batch(insts)
+    S = 10
+    ws = torch.empty(api.batched_workspace_size(len(insts), packed[5], S, packed[0].dtype), dtype=torch.uint8,
+                     device="cuda")
+    stream = torch.cuda.current_stream()
+    times = []
+    for it in range(args.warmup + args.steps):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        api.low_spectrum_batched(*packed[:5], S, n_max=packed[5], workspace=ws, check=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            times.append(ev0.elapsed_time(ev1) / 1e3)
+    t = float(np.median(times))
+    configs = float(sum(2.0 ** J.shape[0] for J, _, _ in insts))
+    print(json.dumps({"metric": "batched instances/s (exact top-S)", "value": len(insts) / t, "unit": "instances/s",
+                      "configs_per_s": configs / t, "ms_per_step": t * 1e3, "steps": args.steps,
+                      "warmup": args.warmup, "config": {"workload": "batched_4096", "S": S}}), flush=True)
+    return 0
+
+
+def qubo_bench(args):
+    """Throughput of the QUBO form (Eqs. (2)-(3)): integer a_ij, b_i uniform in [-9, 9] on n spins,
+    S = 100, one public-API call per step (exact map onto the Gray walk).  One JSON line with the
+    walk kernel's roofline and the oracle's QUBO enumeration on a 2^22 subspace as cpu_baseline."""
+    import torch
+    from paper_1904_03621_gb300 import build
+    build.build()
+    from paper_1904_03621_gb300 import api
+    n = int(args.qubo)
+    rng = np.random.default_rng(0)
+    a = rng.integers(-9, 10, (n, n)).astype(np.int32)
+    b = rng.integers(-9, 10, n).astype(np.int32)
+    ad, bd = torch.tensor(a, device="cuda"), torch.tensor(b, device="cuda")
+    S = 100
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(0)
+    times, kern = [], []
+    for it in range(args.warmup + args.steps):
+        if it == args.warmup:
+            sampler.start()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        api.low_spectrum_qubo(ad, bd, S, check=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            times.append(ev0.elapsed_time(ev1) / 1e3)
+    clocks = sampler.stop() or {}
+    t = float(np.median(times))
+    import oracle
+    o = oracle.get()
+    fb = max(n - 22, 0)
+    t0 = time.perf_counter()
+    o.qubo_low_spectrum(a, b, S, fixed_bits=fb, fixed_value=(1 << fb) // 3 if fb else 0)
+    dt_cpu = time.perf_counter() - t0
+    configs = 2.0 ** n
+    print(json.dumps({"metric": "QUBO configurations/s (exact top-S)", "value": configs / t, "unit": "configs/s",
+                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+                      "higher_is_better": True, "dtype": "i32", "data": "synthetic",
+                      "config": {"workload": f"qubo_int_n{n}", "n": n, "S": S, "configs_per_step": configs},
+                      "clocks": clocks,
+                      "cpu_baseline": {"value": 2.0 ** (n - fb) / dt_cpu, "unit": "configs/s", "cores": o.num_threads,
+                                       "kind": "oracle",
+                                       "sample": f"one subspace of 2^{n - fb} configurations, S={S}, {dt_cpu:.1f} s"}}),
+          flush=True)
+    return 0
+
+
+def checkpoint_bench(args):
+    """Cost of checkpointed search: n = 44 float instance (J ~ N(0,1), h ~ N(0,0.1^2)), S = 1000,
+    split into 2^chunk_bits chunks by the resumable cursor (one device-to-host list copy, host merge
+    and cursor reseal per chunk), against one call over the whole space.  Results must be equal."""
+    import torch
+    from paper_1904_03621_gb300 import build, instances
+    build.build()
+    from paper_1904_03621_gb300 import api
+    from paper_1904_03621_gb300.checkpoint import ResumableSearch
+    cb = int(args.checkpoint)
+    J, h = instances.dense_gaussian(44, 0, h_std=0.1)
+    Jd, hd = torch.tensor(J, device="cuda"), torch.tensor(h, device="cuda")
+    S = 1000
+    api.low_spectrum(Jd, hd, S)                       # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e1, s1 = api.low_spectrum(Jd, hd, S)
+    torch.cuda.synchronize()
+    t_single = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    rs = ResumableSearch(Jd, hd, S, chunk_bits=cb)
+    rs.run()
+    e2, s2 = rs.result()
+    t_chunked = time.perf_counter() - t0
+    same = bool(np.array_equal(e1.cpu().numpy(), e2) and np.array_equal(api.states_u64(s1), s2))
+    print(json.dumps({"metric": "checkpointed search time / single-call time", "value": t_chunked / t_single,
+                      "unit": "ratio", "higher_is_better": False, "single_s": t_single, "chunked_s": t_chunked,
+                      "chunks": 1 << cb, "identical_results": same,
+                      "config": {"workload": "dense_gaussian n=44, S=1000", "chunk_bits": cb}}), flush=True)
+    return 0 if same else 1
 
 
 def main():
@@ -381,9 +507,20 @@ def main():
     ap.add_argument("--fig3-max-n", type=int, default=50)
     ap.add_argument("--potts", default=None, metavar="Q,N",
                     help="throughput of the q-state Potts search on a q^N space instead of the benchmark line")
+    ap.add_argument("--qubo", default=None, metavar="N", help="throughput of the integer QUBO form on N spins")
+    ap.add_argument("--checkpoint", default=None, metavar="CHUNK_BITS",
+                    help="cost of the checkpointed (chunked) search against one call, n = 44")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="time only the 4096-instance batched search (one JSON line)")
     args = ap.parse_args()
     if args.fig3:
         return fig3_sweep(args)
+    if args.batched_only:
+        return batched_only(args)
+    if args.qubo:
+        return qubo_bench(args)
+    if args.checkpoint:
+        return checkpoint_bench(args)
     if args.potts:
         return potts_bench(args)
 
