@@ -447,7 +447,7 @@ bf_status potts_plan(int n, int q, int S, int dtype, const bf_options* opt, Pott
     if (bps < 1) return fail(BF_EUNSUPPORTED, "Potts walk kernel does not fit on an SM (S=%d)", S);
     pl.grid = o.grid_blocks ? o.grid_blocks : sms * bps;
     // enough tasks for ~4 per walk slot, middle digits for the rest (per-thread tables: m q <= 24)
-    const unsigned long long want = (unsigned long long)pl.grid * 256ull * 4ull;
+    const unsigned long long want = (unsigned long long)pl.grid * 256ull * bf::kPottsWalks * 4ull;
     int tdig = 0;
     for (unsigned long long c = 1; c < want && tdig < outer; c *= (unsigned long long)q) tdig++;
     int m = outer - tdig;
@@ -503,8 +503,9 @@ bf_status bf_low_spectrum_potts(const void* J, const void* h, int n, int q, int 
     cudaError_t e = bf::launch_potts_prep(J, h, n, q, (int)dtype, prep, hdr, stream);
     if (e != cudaSuccess) return cuda_fail(e, "Potts prep kernel");
     // per-instance constants become kernel parameters of the walk
-    struct { int q, status, qs, W; double delta, emax; int dT[bf::kPottsMaxSteps]; } hp;
+    struct { int q, status, qs, W; double delta, emax; int dT[bf::kPottsMaxSteps]; unsigned dT16[bf::kPottsMaxSteps]; } hp;
     static_assert(offsetof(bf::PottsPrep, dT) == 32, "PottsPrep header layout");
+    static_assert(offsetof(bf::PottsPrep, dT16) == 32 + 4 * bf::kPottsMaxSteps, "PottsPrep header layout");
     e = cudaMemcpyAsync(&hp, prep, sizeof(hp), cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return cuda_fail(e, "Potts prep copy");
@@ -525,6 +526,7 @@ bf_status bf_low_spectrum_potts(const void* J, const void* h, int n, int q, int 
 
     bf::PottsParams pp{};
     std::memcpy(pp.dT, hp.dT, sizeof(pp.dT));
+    std::memcpy(pp.dT16, hp.dT16, sizeof(pp.dT16));
     for (int i = 0; i <= bf::kMaxN; i++) pp.qpow[i] = i <= n ? bf::potts_pow(q, i) : 0ull;
     pp.n = n;
     pp.q = q;

@@ -184,7 +184,8 @@ struct TcParams {                   // tensor-core screening kernel (k_tc.cu)
 
 constexpr int kPottsMinQ = 2, kPottsMaxQ = 8;
 constexpr int kPottsMaxSteps = 1024;              // configurations of one inner block (q^B)
-constexpr int kPottsMidTable = 24;                // max m * q (per-thread middle-spin tables)
+constexpr int kPottsMidTable = 16;                // max m * q (per-walk middle-digit tables)
+constexpr int kPottsWalks = 2;                    // walks per thread: two 16-bit lanes of one register
 
 // inner digits walked by the unrolled block for q states (q^B <= kPottsMaxSteps)
 __host__ __device__ constexpr int potts_inner_digits(int q)
@@ -219,12 +220,14 @@ struct PottsPrep {                       // written by potts_prep_kernel (device
     int q, status, qs, W;                // states, status bits, scale exponent, window
     double delta, emax;
     int dT[kPottsMaxSteps];              // inner pair-table difference of Gray step t (t >= 1)
+    unsigned dT16[kPottsMaxSteps];       // floor(T / 2^16) differences, same value in both 16-bit lanes
     int Jq[kMaxN * kMaxN];               // quantised symmetric couplings, zero diagonal
     int hq[kMaxN * kPottsMaxQ];          // quantised fields h_i(v), row stride q
 };
 
 struct PottsParams {
     int dT[kPottsMaxSteps];              // copy of PottsPrep::dT (kernel-parameter constants)
+    unsigned dT16[kPottsMaxSteps];       // copy of PottsPrep::dT16
     unsigned long long qpow[kMaxN + 1];  // q^i
     int n, q, B, m;                      // spins, states, inner digits, walked middle digits
     unsigned long long ntasks;           // q^(n - B - m)

@@ -17,12 +17,13 @@
 //     f_k(v) = h_k(v) + sum_{l >= B} J_kl [v == sigma_l],
 //     T[x] = sum_{k<k'<B} J_kk' [x_k == x_k'] ,
 // so a step changing digit k from a to a +- 1 adds +-G_k(min(a, a')) + dT_t with
-// G_k(v) = f_k(v+1) - f_k(v) (registers) and dT_t = T[x_t] - T[x_{t-1}] (kernel
-// parameters): one IADD3 per configuration, a 3-input minimum per two.  A
-// middle-digit change p: a -> a' shifts E_base by C_p(a') - C_p(a) + h_p(a') -
-// h_p(a) (C_p(v) = sum_{l != p} J_pl [sigma_l == v], inner digits at 0) and
-// updates four G entries per inner digit and two C entries per other middle
-// digit (per-thread tables in shared memory).
+// G_k(v) = f_k(v+1) - f_k(v) and dT_t = T[x_t] - T[x_{t-1}].  The unrolled walk runs
+// on 16-bit views of two walks packed in one register (see potts_walk_kernel): one
+// IADD3 per step for both walks (kernel-parameter dT16 constants), one 3-input 16x2
+// minimum per two steps.  A middle-digit change p: a -> a' shifts E_base by
+// C_p(a') - C_p(a) + h_p(a') - h_p(a) (C_p(v) = sum_{l != p} J_pl [sigma_l == v], inner
+// digits at 0) and updates four G entries per inner digit and two C entries per other
+// middle digit (per-walk tables in shared memory).
 //
 // Arithmetic: exact int32 fixed point as for the Ising search (scale 2^qs,
 // |E_q| <= 2^29, residual bound delta, window W, FP64 rescoring of float
@@ -138,7 +139,7 @@ __global__ void __launch_bounds__(kPottsPrepThreads) potts_prep_kernel(const voi
     // dT_t = T[x_t] - T[x_{t-1}] over the inner Gray block (needs Jq: written above by this block)
     const int P = (int)potts_pow(q, B);
     for (int t = tid; t < kPottsMaxSteps; t += blockDim.x) {
-        int d = 0;
+        int d = 0, d16 = 0;
         if (t >= 1 && t < P && n >= B) {
             int T1 = 0, T0 = 0;
             for (int k = 0; k < B; k++)
@@ -148,8 +149,10 @@ __global__ void __launch_bounds__(kPottsPrepThreads) potts_prep_kernel(const voi
                     if (potts_gray_digit(t - 1, q, k) == potts_gray_digit(t - 1, q, k2)) T0 += jv;
                 }
             d = T1 - T0;
+            d16 = (T1 >> 16) - (T0 >> 16);           // floor(T / 2^16) differences telescope exactly
         }
         out->dT[t] = d;
+        out->dT16[t] = (unsigned)d16 * 65537u;       // the same increment in both 16-bit lanes
     }
     if (tid == 0) {
         int status = s_status;
@@ -236,33 +239,42 @@ __global__ void __launch_bounds__(kPottsSeedThreads) potts_seed_kernel(const Pot
 struct PottsSmem {
     int* Jq;                  // n*n
     int* hq;                  // n*q
-    int* Gt;                  // [B*(Q-1)][threads]: G_k(v) of each thread's walk
-    int* Ct;                  // [m*Q][threads]: C_p(v) of each thread's middle digits
+    int* Gt;                  // [walk][B*(Q-1)][threads]: exact G_k(v) of each walk
+    int* Ct;                  // [walk][m*Q][threads]: exact C_p(v) of each walk's middle digits
     int* E;                   // 2*cap
     unsigned long long* C;    // 2*cap
 };
 
+// integer packing hi * 2^16 + lo of two signed 16-bit increments
+__device__ __forceinline__ unsigned pack2(int lo, int hi) { return ((unsigned)hi << 16) + (unsigned)lo; }
+
+// 16-bit views floor((E + 2^31) / 2^16) of two energies in one register
+__device__ __forceinline__ unsigned pack_e16(int lo, int hi)
+{
+    return (((unsigned)hi + 0x80000000u) & 0xffff0000u) | (((unsigned)lo + 0x80000000u) >> 16);
+}
+
 template <int Q, int B, int t>
-__device__ __forceinline__ void potts_step(unsigned& E, unsigned& e1, int& mn, const int (&G)[B][Q - 1],
+__device__ __forceinline__ void potts_step(unsigned& X, unsigned& X1, unsigned& M, const unsigned (&G)[B][Q - 1],
                                            const PottsParams& p)
 {
     constexpr int k = potts_qval(t, Q);
     constexpr int a0 = potts_gray_digit(t - 1, Q, k), a1 = potts_gray_digit(t, Q, k);
     constexpr bool up = a1 > a0;
     constexpr int v = up ? a0 : a1;
-    E += (up ? (unsigned)G[k][v] : 0u - (unsigned)G[k][v]) + (unsigned)p.dT[t];
+    X += (up ? G[k][v] : 0u - G[k][v]) + p.dT16[t];
     if constexpr ((t & 1) != 0) {
-        e1 = E;
+        X1 = X;
     } else {
-        mn = __vimin3_s32(mn, (int)e1, (int)E);
+        M = __vminu2(__vminu2(M, X1), X);
     }
 }
 
 template <int Q, int B, int... Ts>
-__device__ __forceinline__ void potts_block(unsigned& E, unsigned& e1, int& mn, const int (&G)[B][Q - 1],
+__device__ __forceinline__ void potts_block(unsigned& X, unsigned& X1, unsigned& M, const unsigned (&G)[B][Q - 1],
                                             const PottsParams& p, std::integer_sequence<int, Ts...>)
 {
-    (potts_step<Q, B, Ts + 1>(E, e1, mn, G, p), ...);
+    (potts_step<Q, B, Ts + 1>(X, X1, M, G, p), ...);
 }
 
 __device__ __forceinline__ void potts_record(const PottsParams& p, const PottsSmem& s, unsigned* buf_count, int e,
@@ -283,20 +295,29 @@ __device__ __forceinline__ void potts_record(const PottsParams& p, const PottsSm
     }
 }
 
+// Each thread walks two tasks at once: their 16-bit energy views share one register, so one
+// IADD3 advances both and one 3-input 16x2 minimum folds two steps.  A digit's increment is
+// the difference of the floors of its cumulative field offset F_k(v) = f_k(v) - f_k(0), so the
+// views telescope exactly and, as for the Ising walk,
+//     E/2^16 - (B + 2) < x - 2^15 <= E/2^16 + 1 ,
+// and x <= floor((tau + 2^31) / 2^16) + 1 catches every E <= tau.  Flagged walks are
+// rescanned exactly from their int32 tables.
 template <int Q>
 __global__ void __launch_bounds__(kPottsThreads, 2) potts_walk_kernel(const __grid_constant__ PottsParams p)
 {
     constexpr int B = potts_inner_digits(Q);
     constexpr int P = (int)potts_pow(Q, B);
     constexpr int NG = B * (Q - 1);
+    constexpr int NW = kPottsWalks;
+    static_assert(NW == 2, "two walks: the two 16-bit lanes of one register");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = p.n, m = p.m, cap = p.list_cap;
     PottsSmem s;
     s.C = reinterpret_cast<unsigned long long*>(smem_raw);
     s.E = reinterpret_cast<int*>(s.C + 2 * cap);
     s.Gt = s.E + 2 * cap;
-    s.Ct = s.Gt + NG * kPottsThreads;
-    s.Jq = s.Ct + kPottsMidTable * kPottsThreads;
+    s.Ct = s.Gt + NW * NG * kPottsThreads;
+    s.Jq = s.Ct + NW * kPottsMidTable * kPottsThreads;
     s.hq = s.Jq + n * n;
 
     __shared__ unsigned s_buf_count;
@@ -319,11 +340,13 @@ __global__ void __launch_bounds__(kPottsThreads, 2) potts_walk_kernel(const __gr
     const unsigned long long nblocks = p.qpow[m];
     const unsigned long long seg_mask = (1ull << p.seg_log2) - 1ull;
     const unsigned long long task_mul = p.qpow[B + m];
-    int* Gt = s.Gt + tid;                          // entry e at Gt[e * kPottsThreads]
+    // entry e of walk w at table[(w * entries + e) * kPottsThreads]
+    int* Gt = s.Gt + tid;
     int* Ct = s.Ct + tid;
 
     int tau_scr = 0, tie_E = kEmptyE;
     unsigned long long tie_C = kEmptyC;
+    unsigned thr16 = 0u;
     auto refresh = [&]() {
         const int tg = *(volatile int*)&p.hdr->tau;
         const int t = min(s_kE, tg);
@@ -332,25 +355,33 @@ __global__ void __launch_bounds__(kPottsThreads, 2) potts_walk_kernel(const __gr
         long long ts = (long long)t + W;
         if (ts > (1ll << 30)) ts = 1ll << 30;
         tau_scr = (int)ts;
+        const unsigned th = (((unsigned)tau_scr + 0x80000000u) >> 16) + 1u;
+        thr16 = th > 0xffffu ? 0xffffu : th;
     };
     refresh();
 
     for (;;) {
-        if (tid == 0) s_batch = atomicAdd(&p.hdr->task_next, (unsigned long long)kPottsThreads);
+        if (tid == 0) s_batch = atomicAdd(&p.hdr->task_next, (unsigned long long)(NW * kPottsThreads));
         __syncthreads();
         const unsigned long long base = s_batch;
         __syncthreads();
         if (base >= p.ntasks) break;
-        unsigned long long task = base + (unsigned long long)tid;
-        const bool active = task < p.ntasks;
-        if (!active) task = 0;                      // a valid walk whose hits are ignored
-        const unsigned long long c0 = task * task_mul;
+        bool active[NW];
+        unsigned long long c0[NW];
+        unsigned Ebase[NW];
+#pragma unroll
+        for (int w = 0; w < NW; w++) {
+            unsigned long long task = base + (unsigned long long)(NW * tid + w);
+            active[w] = task < p.ntasks;
+            if (!active[w]) task = 0;               // a valid walk whose hits are ignored
+            c0[w] = task * task_mul;
+        }
 
-        // ---- state at the start of the task (inner and middle digits 0)
-        unsigned Ebase;
-        {
+        // ---- state at the start of the task (inner and middle digits 0), per walk
+#pragma unroll 1
+        for (int w = 0; w < NW; w++) {
             unsigned char d[kMaxN];
-            unsigned long long x = c0;
+            unsigned long long x = c0[w];
             for (int i = 0; i < n; i++) {
                 d[i] = (unsigned char)(x % (unsigned long long)Q);
                 x /= (unsigned long long)Q;
@@ -361,7 +392,7 @@ __global__ void __launch_bounds__(kPottsThreads, 2) potts_walk_kernel(const __gr
                 for (int j = i + 1; j < n; j++)
                     if (d[i] == d[j]) e += (unsigned)s.Jq[i * n + j];
             }
-            Ebase = e;
+            Ebase[w] = e;
             // G_k(v) = f_k(v+1) - f_k(v), f_k(v) = h_k(v) + sum_{l >= B} J_kl [v == d_l]
             for (int k = 0; k < B; k++) {
                 int f[Q];
@@ -373,7 +404,7 @@ __global__ void __launch_bounds__(kPottsThreads, 2) potts_walk_kernel(const __gr
                     for (int v = 0; v < Q; v++) f[v] += (d[l] == v) ? jv : 0;
                 }
 #pragma unroll
-                for (int v = 0; v < Q - 1; v++) Gt[(k * (Q - 1) + v) * kPottsThreads] = f[v + 1] - f[v];
+                for (int v = 0; v < Q - 1; v++) Gt[(w * NG + k * (Q - 1) + v) * kPottsThreads] = f[v + 1] - f[v];
             }
             // C_p(v) = sum_{l != B+p} J_{B+p, l} [d_l == v] for the middle digits
             for (int pm = 0; pm < m; pm++) {
@@ -388,27 +419,38 @@ __global__ void __launch_bounds__(kPottsThreads, 2) potts_walk_kernel(const __gr
                     for (int v = 0; v < Q; v++) cv[v] += (d[l] == v) ? jv : 0;
                 }
 #pragma unroll
-                for (int v = 0; v < Q; v++) Ct[(pm * Q + v) * kPottsThreads] = cv[v];
+                for (int v = 0; v < Q; v++) Ct[(w * kPottsMidTable + pm * Q + v) * kPottsThreads] = cv[v];
             }
         }
 
         for (unsigned long long u = 0; u < nblocks; ++u) {
-            // ---- one block of q^B configurations
-            int G[B][Q - 1];
+            // ---- one block of q^B configurations for both walks
+            unsigned G[B][Q - 1];
 #pragma unroll
-            for (int k = 0; k < B; k++)
+            for (int k = 0; k < B; k++) {
+                int F0 = 0, F1 = 0;                     // cumulative F_k(v) of the two walks
 #pragma unroll
-                for (int v = 0; v < Q - 1; v++) G[k][v] = Gt[(k * (Q - 1) + v) * kPottsThreads];
-            unsigned E = Ebase, e1 = Ebase;
-            int mn = (int)Ebase;
-            potts_block<Q, B>(E, e1, mn, G, p, std::make_integer_sequence<int, P - 1>{});
-            mn = min(mn, (int)e1);
-            if (active && mn <= tau_scr) {
-                // exact rescan of the block
+                for (int v = 0; v < Q - 1; v++) {
+                    const int n0 = F0 + Gt[(0 * NG + k * (Q - 1) + v) * kPottsThreads];
+                    const int n1 = F1 + Gt[(1 * NG + k * (Q - 1) + v) * kPottsThreads];
+                    G[k][v] = pack2((n0 >> 16) - (F0 >> 16), (n1 >> 16) - (F1 >> 16));
+                    F0 = n0;
+                    F1 = n1;
+                }
+            }
+            unsigned X = pack_e16((int)Ebase[0], (int)Ebase[1]);
+            unsigned X1 = X, M = X;
+            potts_block<Q, B>(X, X1, M, G, p, std::make_integer_sequence<int, P - 1>{});
+            M = __vminu2(M, X1);
+            const bool flag[NW] = {active[0] && (M & 0xffffu) <= thr16, active[1] && (M >> 16) <= thr16};
+#pragma unroll 1
+            for (int w = 0; w < NW; w++) {
+                if (!flag[w]) continue;
+                // exact rescan of walk w's block
                 unsigned long long mid = 0ull;
                 for (int pm = 0; pm < m; pm++) mid += (unsigned long long)potts_gray_digit(u, Q, pm) * p.qpow[pm];
-                const unsigned long long cb = c0 + mid * p.qpow[B];
-                unsigned e = Ebase;
+                const unsigned long long cb = c0[w] + mid * p.qpow[B];
+                unsigned e = Ebase[w];
                 unsigned long long x = 0ull;
                 for (int t = 0; t < P; t++) {
                     if (t > 0) {
@@ -416,7 +458,7 @@ __global__ void __launch_bounds__(kPottsThreads, 2) potts_walk_kernel(const __gr
                         const int a0 = potts_gray_digit((unsigned long long)(t - 1), Q, k);
                         const int a1 = potts_gray_digit((unsigned long long)t, Q, k);
                         const bool up = a1 > a0;
-                        const unsigned g = (unsigned)Gt[(k * (Q - 1) + (up ? a0 : a1)) * kPottsThreads];
+                        const unsigned g = (unsigned)Gt[(w * NG + k * (Q - 1) + (up ? a0 : a1)) * kPottsThreads];
                         e += (up ? g : 0u - g) + (unsigned)p.dT[t];
                         x = up ? x + p.qpow[k] : x - p.qpow[k];
                     }
@@ -467,27 +509,31 @@ __global__ void __launch_bounds__(kPottsThreads, 2) potts_walk_kernel(const __gr
                 refresh();
             }
 
-            // ---- change one middle digit: pm = q-adic valuation of u + 1, a -> a'
+            // ---- change one middle digit: pm = q-adic valuation of u + 1, a -> a2 (both walks)
             if (u + 1 < nblocks) {
                 const int pm = potts_qval(u + 1, Q);
                 const int a = potts_gray_digit(u, Q, pm), a2 = potts_gray_digit(u + 1, Q, pm);
                 const int sp = B + pm;
-                Ebase += (unsigned)(Ct[(pm * Q + a2) * kPottsThreads] - Ct[(pm * Q + a) * kPottsThreads]) +
-                         (unsigned)(s.hq[sp * Q + a2] - s.hq[sp * Q + a]);
-                for (int k = 0; k < B; k++) {
-                    const int jv = s.Jq[k * n + sp];
-                    int* g = Gt + k * (Q - 1) * kPottsThreads;
-                    // f_k(a) -= J, f_k(a2) += J
-                    if (a >= 1) g[(a - 1) * kPottsThreads] -= jv;
-                    if (a <= Q - 2) g[a * kPottsThreads] += jv;
-                    if (a2 >= 1) g[(a2 - 1) * kPottsThreads] += jv;
-                    if (a2 <= Q - 2) g[a2 * kPottsThreads] -= jv;
-                }
-                for (int p2 = 0; p2 < m; p2++) {
-                    if (p2 == pm) continue;
-                    const int jv = s.Jq[(B + p2) * n + sp];
-                    Ct[(p2 * Q + a) * kPottsThreads] -= jv;
-                    Ct[(p2 * Q + a2) * kPottsThreads] += jv;
+#pragma unroll
+                for (int w = 0; w < NW; w++) {
+                    int* C = Ct + w * kPottsMidTable * kPottsThreads;
+                    Ebase[w] += (unsigned)(C[(pm * Q + a2) * kPottsThreads] - C[(pm * Q + a) * kPottsThreads]) +
+                                (unsigned)(s.hq[sp * Q + a2] - s.hq[sp * Q + a]);
+                    for (int k = 0; k < B; k++) {
+                        const int jv = s.Jq[k * n + sp];
+                        int* g = Gt + (w * NG + k * (Q - 1)) * kPottsThreads;
+                        // f_k(a) -= J, f_k(a2) += J
+                        if (a >= 1) g[(a - 1) * kPottsThreads] -= jv;
+                        if (a <= Q - 2) g[a * kPottsThreads] += jv;
+                        if (a2 >= 1) g[(a2 - 1) * kPottsThreads] += jv;
+                        if (a2 <= Q - 2) g[a2 * kPottsThreads] -= jv;
+                    }
+                    for (int p2 = 0; p2 < m; p2++) {
+                        if (p2 == pm) continue;
+                        const int jv = s.Jq[(B + p2) * n + sp];
+                        C[(p2 * Q + a) * kPottsThreads] -= jv;
+                        C[(p2 * Q + a2) * kPottsThreads] += jv;
+                    }
                 }
             }
         }
@@ -503,8 +549,8 @@ __global__ void __launch_bounds__(kPottsThreads, 2) potts_walk_kernel(const __gr
 size_t potts_walk_smem(int q, int n, int list_cap)
 {
     const int B = potts_inner_digits(q);
-    return (size_t)2 * list_cap * 12 + (size_t)B * (q - 1) * kPottsThreads * 4 +
-           (size_t)kPottsMidTable * kPottsThreads * 4 + (size_t)n * n * 4 + (size_t)n * q * 4;
+    return (size_t)2 * list_cap * 12 + (size_t)kPottsWalks * B * (q - 1) * kPottsThreads * 4 +
+           (size_t)kPottsWalks * kPottsMidTable * kPottsThreads * 4 + (size_t)n * n * 4 + (size_t)n * q * 4;
 }
 
 template <int Q>
