@@ -102,6 +102,7 @@ bf_status make_plan(int n, int S, int dtype, const bf_options* opt, Plan& pl)
     if (e != cudaSuccess) return cuda_fail(e, "device query");
     pl.list_cap = bf::list_capacity(S);
     pl.variant = o.variant == BF_VARIANT_TC ? BF_VARIANT_TC : BF_VARIANT_GRAY;
+    int full_grid = 1;
     if (pl.variant == BF_VARIANT_TC) {
         // one 256-thread block per SM (each holds all 512 TMEM columns); a task is 2^m tiles
         if (free_bits < 15) return fail(BF_EUNSUPPORTED, "the tensor-core variant needs n - fixed_bits >= 15");
@@ -117,6 +118,9 @@ bf_status make_plan(int n, int S, int dtype, const bf_options* opt, Plan& pl)
         }
         pl.nh = outer - pl.m;
         pl.seg_log2 = std::min(pl.m, 4);
+        // a block takes one task at a time: no more blocks than tasks
+        full_grid = pl.grid;
+        if (!o.grid_blocks && pl.nh < 30) pl.grid = (int)std::min<unsigned long long>(pl.grid, 1ull << pl.nh);
     } else {
         int bps = bf::gray_blocks_per_sm(pl.list_cap);
         if (bps < 1) return fail(BF_ECUDA, "enumeration kernel does not fit on an SM (S=%d)", S);
@@ -131,14 +135,24 @@ bf_status make_plan(int n, int S, int dtype, const bf_options* opt, Plan& pl)
         }
         pl.nh = walk_bits - pl.m;
         pl.seg_log2 = std::min(pl.m, 4);
+        // a block takes kGrayThreads * kWalks tasks at a time: small searches need fewer blocks,
+        // and every block's list goes through the merge tree
+        full_grid = pl.grid;
+        if (!o.grid_blocks && pl.nh < 40) {
+            const unsigned long long per_block = (unsigned long long)bf::kGrayThreads * bf::kWalks;
+            const unsigned long long need = ((1ull << pl.nh) + per_block - 1) / per_block;
+            pl.grid = (int)std::min<unsigned long long>(pl.grid, need);
+        }
     }
-    // seed: a pseudo-random sample of up to 2^20 configurations, one sorted list per block
+    // seed: a pseudo-random sample of up to 2^20 configurations, one sorted list per seed block;
+    // sized by the device-filling grid even when the walk needs fewer blocks, so that small
+    // searches start from the same threshold quality
     pl.seed_per_block = std::max(pl.list_cap, 2048);
     unsigned long long sample = 1ull << std::min(free_bits, bf::kSeedLog2);
-    sample = std::min(sample, (unsigned long long)pl.grid * pl.seed_per_block);
+    sample = std::min(sample, (unsigned long long)full_grid * pl.seed_per_block);
     pl.seed_sample = sample;
     pl.seed_blocks = (int)((sample + pl.seed_per_block - 1) / pl.seed_per_block);
-    pl.L = bf::make_layout(S, pl.grid, o.spill_log2 ? o.spill_log2 : 21);
+    pl.L = bf::make_layout(S, std::max(pl.grid, pl.seed_blocks), o.spill_log2 ? o.spill_log2 : 21);
     pl.bytes = pl.L.total;
     return BF_OK;
 }
