@@ -112,6 +112,9 @@ __device__ __forceinline__ void mbar_arrive(uint32_t addr)
 // named barrier of the epilogue warps (the MMA warp does not take part)
 __device__ __forceinline__ void ep_sync() { asm volatile("bar.sync 1, %0;" :: "n"(kTcEpThreads) : "memory"); }
 
+// minimum over 128 consecutive accumulator columns of this thread's TMEM lane:
+// four reducing loads of 32 columns and one wait, inside one asm block so that
+// the loaded (unused) registers are private to it
 __device__ __forceinline__ float tmem_min128(uint32_t taddr)
 {
     float m0, m1, m2, m3;
