@@ -701,7 +701,7 @@ extern "C" {
 
 size_t bf_batched_workspace_size(int B, int n_max, int S, bf_dtype dtype, const bf_options* opt)
 {
-    BPlan bp;
+    BPlan bp{};
     const bf_options o = effective_batched_options(B, n_max, S, dtype, opt);
     if (make_bplan(B, n_max, S, dtype, &o, bp) != BF_OK) return 0;
     return bp.total;
@@ -713,7 +713,7 @@ bf_status bf_low_spectrum_batched(int B, const void* J_packed, const int64_t* J_
                                   const bf_options* opt, void* stream_ptr)
 {
     g_detail.clear();
-    BPlan bp;
+    BPlan bp{};
     const bf_options eff = effective_batched_options(B, n_max, S, dtype, opt);
     bf_status st = make_bplan(B, n_max, S, dtype, &eff, bp);
     if (st != BF_OK) return st;
@@ -844,7 +844,7 @@ extern "C" bf_status bf_autotune_batched(int B, const void* J_packed, const int6
             bf_options o{};
             o.task_log2 = tl;
             o.grid_blocks = sms * per_sm;
-            BPlan bp;
+            BPlan bp{};
             if (make_bplan(B, n_max, S, dtype, &o, bp) != BF_OK) continue;
             if (bp.total > workspace_bytes) continue;       // candidate needs a larger pool
             // one untimed run, then one timed run of the whole batched call
