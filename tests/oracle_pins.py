@@ -9,7 +9,6 @@ functions run against copies of the oracle with planted mistakes
 from __future__ import annotations
 
 import itertools
-import math
 import os
 
 import numpy as np

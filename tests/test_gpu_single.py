@@ -177,7 +177,6 @@ def test_invalid_arguments(bf):
     lib = _lib.load()
     en = torch.empty(10, dtype=torch.float64, device="cuda")
     st = torch.empty(10, dtype=torch.int64, device="cuda")
-    import ctypes
     s = lib.bf_low_spectrum(J.data_ptr(), h.data_ptr(), 20, 10, _lib.BF_F64, en.data_ptr(), st.data_ptr(),
                             ws.data_ptr(), 1024, None, None)
     assert s == _lib.BF_EWORKSPACE
