@@ -89,6 +89,11 @@ typedef enum {
  *                in tests
  *   profile      nonzero: record CUDA events around the enumeration kernel on
  *                the call's stream (read back with bf_last_profile)
+ *   stall_test   testing only: nonzero makes the tensor-core kernel's MMA warps
+ *                issue nothing, so the epilogue's bounded waits (0.2 s) run out;
+ *                the kernel then stops, frees its tensor memory and the call's
+ *                workspace status is BF_ETIMEOUT.  The CUDA context stays
+ *                usable.  Ignored by the other kernels.
  */
 typedef struct {
     int32_t variant;
@@ -98,7 +103,8 @@ typedef struct {
     int32_t grid_blocks;
     int32_t spill_log2;
     int32_t profile;
-    int32_t reserved[6];
+    int32_t stall_test;
+    int32_t reserved[5];
 } bf_options;
 
 /* Largest S accepted by bf_low_spectrum. */

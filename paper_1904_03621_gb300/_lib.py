@@ -26,7 +26,7 @@ EXPORTS = ["bf_workspace_size", "bf_low_spectrum", "bf_low_spectrum_noalloc", "b
 class Options(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("fixed_bits", ctypes.c_int32), ("fixed_value", ctypes.c_uint64),
                 ("task_log2", ctypes.c_int32), ("grid_blocks", ctypes.c_int32), ("spill_log2", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("profile", ctypes.c_int32), ("stall_test", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class BFError(RuntimeError):

@@ -20,9 +20,11 @@ def _stream_handle(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _options(variant=0, fixed_bits=0, fixed_value=0, task_log2=0, grid_blocks=0, spill_log2=0, profile=0):
+def _options(variant=0, fixed_bits=0, fixed_value=0, task_log2=0, grid_blocks=0, spill_log2=0, profile=0,
+             stall_test=0):
     return _lib.Options(variant=variant, fixed_bits=fixed_bits, fixed_value=fixed_value,
-                        task_log2=task_log2, grid_blocks=grid_blocks, spill_log2=spill_log2, profile=profile)
+                        task_log2=task_log2, grid_blocks=grid_blocks, spill_log2=spill_log2, profile=profile,
+                        stall_test=stall_test)
 
 
 def workspace_size(n: int, S: int, dtype: torch.dtype, **opts) -> int:
@@ -37,7 +39,7 @@ def workspace_size(n: int, S: int, dtype: torch.dtype, **opts) -> int:
 def low_spectrum(J: torch.Tensor, h: torch.Tensor, S: int, *, variant: int = 0, fixed_bits: int = 0,
                  fixed_value: int = 0, task_log2: int = 0, grid_blocks: int = 0, spill_log2: int = 0,
                  profile: int = 0, stream=None, workspace: torch.Tensor | None = None, check: bool = True,
-                 out: tuple | None = None):
+                 out: tuple | None = None, stall_test: int = 0):
     """S lowest (energy, configuration) pairs of E(s) = sum_{i<j} J_ij s_i s_j + sum_i h_i s_i.
 
     J: (n, n) CUDA tensor (int32, float32 or float64), strict upper triangle read.
@@ -54,7 +56,7 @@ def low_spectrum(J: torch.Tensor, h: torch.Tensor, S: int, *, variant: int = 0, 
     n = J.shape[0]
     J = J.contiguous()
     h = h.contiguous()
-    o = _options(variant, fixed_bits, fixed_value, task_log2, grid_blocks, spill_log2, profile)
+    o = _options(variant, fixed_bits, fixed_value, task_log2, grid_blocks, spill_log2, profile, stall_test)
     nbytes = lib.bf_workspace_size(n, S, _DTYPES[J.dtype], ctypes.byref(o))
     if nbytes == 0:
         # the call validates its arguments before touching any pointer: get the exact status

@@ -324,6 +324,7 @@ bf_status bf_low_spectrum(const void* J, const void* h, int n, int S, bf_dtype d
         tp.spill_cap = L.spill_cap;
         // split residuals <= 2^-18 |x| for 8 values below 2^30, FP32 accumulation and conversions
         tp.delta = 1 << 17;
+        tp.stall_test = opt ? opt->stall_test : 0;
         tp.prep = prep;
         tp.hdr = hdr;
         tp.list_E = AE;

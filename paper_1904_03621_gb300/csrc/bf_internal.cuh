@@ -172,6 +172,7 @@ struct TcParams {                   // tensor-core screening kernel (k_tc.cu)
     int S, list_cap, W, seg_log2;
     unsigned spill_cap;
     int delta;                      // widening of the tensor-core test (quantised units)
+    int stall_test;                 // testing only: the MMA warps issue nothing (bounded waits run out)
     const Prep* prep;
     WsHeader* hdr;
     int* list_E;

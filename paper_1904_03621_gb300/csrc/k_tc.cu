@@ -413,6 +413,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             };
             unsigned u = (mst - it0) & 1u;             // first tile of this stage in the task
+            if (p.stall_test) u = ntiles;              // testing only: issue nothing
             if (u < ntiles) {
                 if (u == 1u) step(1u);
                 publish((it0 + u) & (kTcBBufs - 1));

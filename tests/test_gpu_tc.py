@@ -109,3 +109,18 @@ def test_tc_matches_gray_on_n48_subspaces(bf, o):
         en_g, st_g = run(bf, J, h, 1000, variant=1, fixed_bits=24, fixed_value=v)
         assert np.array_equal(st_t, st_g)
         assert_float_parity(o, J, h, en_t, st_t, gold[v][0], gold[v][1])
+
+
+def test_tc_bounded_wait_reports_timeout(bf, o):
+    """Failure detection without a GPU fault: with stall_test the MMA warps issue nothing, the
+    epilogue's bounded waits (0.2 s) run out, the call reports BF_ETIMEOUT, and the same
+    context then runs a correct search."""
+    import time
+    from paper_1904_03621_gb300 import _lib
+    J, h = instances.dense_gaussian(20, 3)
+    t0 = time.time()
+    with pytest.raises(_lib.BFError) as err:
+        run(bf, J, h, 10, variant=TC, stall_test=1)
+    assert err.value.status == _lib.BF_ETIMEOUT
+    assert time.time() - t0 < 30.0
+    check(bf, o, J, h, 10)
