@@ -60,6 +60,7 @@ struct Plan {
     bool direct;
     int variant;
     int list_cap, grid, m, nh, seg_log2, seed_per_block, seed_blocks, inner_bits;
+    int descent_blocks;             // > 0: local-search seed instead of the sampled one
     unsigned long long seed_sample;
     bf::Layout L;
     size_t bytes;
@@ -152,6 +153,9 @@ bf_status make_plan(int n, int S, int dtype, const bf_options* opt, Plan& pl)
     sample = std::min(sample, (unsigned long long)full_grid * pl.seed_per_block);
     pl.seed_sample = sample;
     pl.seed_blocks = (int)((sample + pl.seed_per_block - 1) / pl.seed_per_block);
+    // beyond 2^kSeedLog2 configurations the sample no longer covers the space: a local search
+    // and the Hamming balls of its lowest minima give a far lower first threshold
+    pl.descent_blocks = free_bits > bf::kSeedLog2 ? std::min(sms, bf::kDescentMaxBlocks) : 0;
     pl.L = bf::make_layout(S, std::max(pl.grid, pl.seed_blocks), o.spill_log2 ? o.spill_log2 : 21);
     pl.bytes = pl.L.total;
     return BF_OK;
@@ -269,14 +273,24 @@ bf_status bf_low_spectrum(const void* J, const void* h, int n, int S, bf_dtype d
     auto* BC = reinterpret_cast<unsigned long long*>(ws + L.listB_C);
     bool in_a = true;
 
-    // seed threshold: S-th lowest quantised energy of a pseudo-random sample
-    e = bf::launch_seed(prep, n, pl.free_bits, pl.hiconst, pl.seed_sample, pl.seed_per_block, pl.seed_blocks,
-                        L.list_cap, AE, AC, stream);
-    if (e != cudaSuccess) return cuda_fail(e, "seed kernel");
-    e = merge_tree(AE, AC, BE, BC, pl.seed_blocks, L.list_cap, S, 0, hdr, stream, in_a);
-    if (e != cudaSuccess) return cuda_fail(e, "seed merge");
-    e = bf::launch_set_tau(in_a ? AE : BE, S, hdr, stream);
-    if (e != cudaSuccess) return cuda_fail(e, "seed threshold");
+    // seed threshold: the S-th lowest quantised energy of a pseudo-random sample, and / or of the
+    // Hamming balls around local-search minima (alone when the first ball holds S configurations)
+    const bool ball_only = pl.descent_blocks && bf::ball_size(pl.free_bits) >= S;
+    if (!ball_only) {
+        e = bf::launch_seed(prep, n, pl.free_bits, pl.hiconst, pl.seed_sample, pl.seed_per_block, pl.seed_blocks,
+                            L.list_cap, AE, AC, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "seed kernel");
+        e = merge_tree(AE, AC, BE, BC, pl.seed_blocks, L.list_cap, S, 0, hdr, stream, in_a);
+        if (e != cudaSuccess) return cuda_fail(e, "seed merge");
+        e = bf::launch_set_tau(in_a ? AE : BE, S, hdr, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "seed threshold");
+    }
+    if (pl.descent_blocks) {
+        e = bf::launch_descent_seed(prep, n, pl.free_bits, pl.hiconst, S, pl.descent_blocks,
+                                    reinterpret_cast<int*>(ws + L.best_E),
+                                    reinterpret_cast<unsigned long long*>(ws + L.best_C), ball_only, hdr, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "local-search seed");
+    }
 
     bf::GrayParams gp{};
     std::memcpy(gp.dT16, hl.dT16, sizeof(gp.dT16));

@@ -36,6 +36,7 @@ constexpr int kWalks = 4;                        // walks (tasks) per thread: tw
 constexpr int kGrayThreads = 256;                // block size of the enumeration kernel
 constexpr int kSmallFreeBits = 12;               // at most 2^12 configurations: direct kernel
 constexpr int kSeedLog2 = 20;                    // at most 2^20 sampled configurations for the seed
+constexpr int kDescentMaxBlocks = 256;           // blocks of the local-search seed (one minimum each)
 constexpr int kMinListCap = 128;
 constexpr int kMaxListCap = 4096;
 constexpr int kEmqLog2 = 29;                     // |E_q|, |local field_q| < 2^29
@@ -93,7 +94,7 @@ constexpr unsigned long long kEmptyC = ~0ull;
 
 // Workspace layout of bf_low_spectrum.
 struct Layout {
-    size_t header, prep, listA_E, listA_C, listB_E, listB_C, spill_E, spill_C, rescore, total;
+    size_t header, prep, listA_E, listA_C, listB_E, listB_C, spill_E, spill_C, rescore, best_E, best_C, total;
     int lists, list_cap;
     unsigned spill_cap;
 };
@@ -132,6 +133,8 @@ __host__ inline Layout make_layout(int S, int max_blocks, int spill_log2)
     L.spill_E = off;  off = align_up(off + (size_t)L.spill_cap * 4, 256);
     L.spill_C = off;  off = align_up(off + (size_t)L.spill_cap * 8, 256);
     L.rescore = off;  off = align_up(off + (size_t)L.list_cap * 8, 256);
+    L.best_E = off;   off = align_up(off + (size_t)kDescentMaxBlocks * 4, 256);
+    L.best_C = off;   off = align_up(off + (size_t)kDescentMaxBlocks * 8, 256);
     L.total = off;
     return L;
 }
@@ -331,6 +334,13 @@ cudaError_t launch_finalize(const int* E, const unsigned long long* C, int cap, 
 cudaError_t launch_seed(const Prep* prep, int n, int free_bits, unsigned long long hiconst,
                         unsigned long long sample, int per_block, int blocks, int cap, int* outE,
                         unsigned long long* outC, cudaStream_t s);
+// Local-search seed (k_descent.cu): `blocks` descent blocks, then the S-th lowest distinct
+// energy of the radius-2 Hamming balls around the lowest minima found becomes hdr->tau
+// (assign; needs ball_size(free_bits) >= S) or lowers it (atomicMin).
+int ball_size(int free_bits);
+cudaError_t launch_descent_seed(const Prep* prep, int n, int free_bits, unsigned long long hiconst, int S,
+                                int blocks, int* bestE, unsigned long long* bestC, bool assign, WsHeader* hdr,
+                                cudaStream_t s);
 // hdr->tau = E[S - 1] of a merged list; resets the task and spill counters.
 cudaError_t launch_set_tau(const int* E, int S, WsHeader* hdr, cudaStream_t s);
 // Small instances (<= 2^kSmallFreeBits configurations): direct enumeration.

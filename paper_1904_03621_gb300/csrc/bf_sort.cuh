@@ -30,7 +30,7 @@ __device__ void group_sort(K* key, unsigned long long* cfg, int len, int t, int 
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
             sync();
             for (int i = t; i < (len >> 1); i += nt) {
-                int lo = 2 * stride * (i / stride) + (i % stride);
+                int lo = ((i & -stride) << 1) + (i & (stride - 1));   // stride is a power of two
                 cmp_swap(key, cfg, lo, lo + stride, (lo & size) == 0);
             }
         }
@@ -60,7 +60,7 @@ __device__ void block_merge_halves(K* key, unsigned long long* cfg, int len)
     for (int stride = half; stride > 0; stride >>= 1) {
         __syncthreads();
         for (int i = threadIdx.x; i < half; i += blockDim.x) {
-            int lo = 2 * stride * (i / stride) + (i % stride);
+            int lo = ((i & -stride) << 1) + (i & (stride - 1));   // stride is a power of two
             cmp_swap(key, cfg, lo, lo + stride, true);
         }
     }

@@ -381,7 +381,7 @@ __device__ void warp_sort(int* E, unsigned long long* C, int len, int lane)
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
             __syncwarp();
             for (int i = lane; i < (len >> 1); i += 32) {
-                int lo = 2 * stride * (i / stride) + (i % stride);
+                int lo = ((i & -stride) << 1) + (i & (stride - 1));   // stride is a power of two
                 cmp_swap(E, C, lo, lo + stride, (lo & size) == 0);
             }
         }

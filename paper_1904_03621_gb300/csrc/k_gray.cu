@@ -17,7 +17,8 @@
 //
 // Arithmetic: the quantised instance is exact in int32.  Per walk we keep
 // E0 (energy with all inner spins at -1), G_k = 2 F_k for the B inner spins
-// (fields from non-inner spins) and the local fields of 4 middle spins.
+// (fields from non-inner spins) and the local fields of 4 middle spins.  A
+// block takes kGrayThreads * kWalks consecutive tasks at a time.
 // Inside a block, E(g) = E0 + sum_{k in g} G_k + T[g] - T[0].  The unrolled
 // walk runs on 16-bit values floor((E + 2^31) / 2^16), two walks packed per
 // 32-bit register: one IADD3 advances two walks by one flip and one 16x2
@@ -25,7 +26,8 @@
 // reaches the threshold is rescanned exactly in int32, and only exact hits
 // are recorded.  Error bound of the 16-bit value x(g) of a configuration:
 //   E(g)/2^16 - (B + 2) < x(g) - 2^15 <= E(g)/2^16 + 1,
-// so x(g) <= floor((tau + 2^31) / 2^16) + 1 catches every E(g) <= tau.
+// so x(g) <= floor((tau + 2^31) / 2^16) + 1 catches every E(g) <= tau.  The
+// warp rescans its flagged walks together, 2^B / 32 configurations per lane.
 //
 // Selection: hits go to a shared-memory buffer (spill area in the
 // workspace when full).  At segment boundaries the block merges the buffer
@@ -39,6 +41,9 @@
 
 namespace bf {
 namespace {
+
+constexpr int kVarBits = 10;   // task-index bits that differ within one batch of tasks
+static_assert(kGrayThreads * kWalks == 1 << kVarBits, "a batch is 2^kVarBits tasks");
 
 __host__ __device__ constexpr int cx_ctz(int t) { return (t & 1) ? 0 : 1 + cx_ctz(t >> 1); }
 // value (1 = +1) of the spin flipped by step t of the reflected Gray code
@@ -80,7 +85,7 @@ __device__ __forceinline__ unsigned pack_energy(int lo, int hi)
 struct Smem {
     int* Jq;                 // n*n
     int* hq;                 // kMaxN
-    int* T;                  // 256
+    int* T;                  // 2^B
     int (*col)[16];          // kMaxN x 16
     int* E;                  // 2 * cap
     unsigned long long* C;   // 2 * cap
@@ -101,6 +106,34 @@ __device__ __forceinline__ void record(const GrayParams& p, const Smem& s, unsig
         p.spill_C[g] = c;
     } else {
         atomicOr(&p.hdr->status, kErrSpill);
+    }
+}
+
+// Exact rescan of one walk's block by a whole warp.  Lane L takes the R = 2^B / 32
+// Gray steps t = L*R .. L*R + R - 1: it sums the fields of its first configuration
+// g(t) = t ^ (t >> 1), then follows one flip per step (step t flips bit ctz(t)).
+// E(g) = ebase + T[g] + sum_{k in g} G_k, with ebase = E0 - T[0]; G is the walk's
+// field row, staged in shared memory by the lane that owns the walk.
+template <int IB>
+__device__ __forceinline__ void warp_rescan(const GrayParams& p, const Smem& s, unsigned* buf_count, unsigned ebase,
+                                            const int* G, unsigned long long cb, int tau, int tie_E,
+                                            unsigned long long tie_C, int lane)
+{
+    constexpr unsigned R = (1u << IB) / 32u;
+    unsigned t = (unsigned)lane * R;
+    unsigned g = t ^ (t >> 1);
+    unsigned sg = 0u;
+#pragma unroll
+    for (int k = 0; k < IB; k++) sg += ((g >> k) & 1u) ? (unsigned)G[k] : 0u;
+    for (unsigned i = 0; i < R; i++) {
+        if (i > 0) {
+            const int k = __ffs(++t) - 1;
+            g ^= 1u << k;
+            sg += ((g >> k) & 1u) ? (unsigned)G[k] : 0u - (unsigned)G[k];
+        }
+        const int e = (int)(ebase + (unsigned)s.T[g] + sg);
+        const unsigned long long c = cb | g;
+        if (e <= tau && !(e == tie_E && c > tie_C)) record(p, s, buf_count, e, c);
     }
 }
 
@@ -129,15 +162,18 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
     s.C = reinterpret_cast<unsigned long long*>(smem_raw);                  // 2*cap
     s.E = reinterpret_cast<int*>(s.C + 2 * cap);                            // 2*cap
     s.col = reinterpret_cast<int(*)[16]>(s.E + 2 * cap);                    // kMaxN*16
-    s.T = reinterpret_cast<int*>(s.col + kMaxN);                            // 256
+    s.T = reinterpret_cast<int*>(s.col + kMaxN);                            // 2^B
     s.hq = s.T + kGrayMaxInnerSteps;                                               // kMaxN
     s.Jq = s.hq + kMaxN;                                                    // n*n
 
     __shared__ unsigned s_buf_count;
     __shared__ int s_list_count, s_kE;               // s_kE, s_kC: S-th record of the block list
     __shared__ unsigned long long s_batch, s_kC;
+    __shared__ int s_ER[2], s_fR[kVarBits], s_gR[IB], s_fmR[kKeep];   // energy and fields of cR
+    __shared__ int s_Gw[kGrayThreads / 32][IB];                         // field row of a walk being rescanned
 
     const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
     const Prep* prep = p.prep;
     for (int i = tid; i < n * n; i += blockDim.x) s.Jq[i] = prep->Jq[i];
     for (int i = tid; i < kMaxN; i += blockDim.x) s.hq[i] = prep->hq[i];
@@ -186,39 +222,156 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
         int E0[kWalks], G[kWalks][IB], Fm[kWalks][kKeep];
         unsigned long long cfg0[kWalks];
         bool active[kWalks];
+        if constexpr (IB < kGrayMaxInnerBits) {
+            // Short tasks (the 9-spin block serves searches below 2^42 configurations, whose
+            // tasks hold few blocks): the setup is shared by the block.
+            // The batch's kGrayThreads * kWalks tasks share every spin except the nv lowest
+            // task-index bits, which walk x = tid * kWalks + w sets to x.  The block first
+            // evaluates cR, the batch's configuration with those nv spins at -1: its energy
+            // and the local fields the walks start from.  Each walk then adds the flips of its
+            // own bits (Eq. (1)): flipping spin v from -1 to +1 adds 2 f_v to E and 2 J_jv to
+            // the field on spin j, and each pair of flipped spins adds 4 J_vv' to E.
+            const int nv = p.nh < kVarBits ? p.nh : kVarBits;
+            const unsigned long long cR = p.hiconst | (base << walk_shift);
+            {
+                int part = 0;
+                if (tid < kMaxN) {
+                    const int i = tid;
+                    if (i < n) {
+                        int row = s.hq[i];
+                        const int* Ji = s.Jq + i * n;
+                        for (int j = i + 1; j < n; j++) {
+                            const int v = Ji[j];
+                            row += ((cR >> j) & 1ull) ? v : -v;
+                        }
+                        part = ((cR >> i) & 1ull) ? row : -row;
+                    }
 #pragma unroll
-        for (int w = 0; w < kWalks; w++) {
-            unsigned long long task = base + (unsigned long long)(tid * kWalks + w);
-            active[w] = task < p.ntasks;
-            if (!active[w]) task = 0;   // a valid walk whose hits are ignored
-            cfg0[w] = p.hiconst | (task << walk_shift);
-        }
-#pragma unroll
-        for (int w = 0; w < kWalks; w++) {
-            const unsigned long long c = cfg0[w];
-            int e = 0;
-            for (int i = 0; i < n; i++) {
-                int row = s.hq[i];
-                const int* Ji = s.Jq + i * n;
-                for (int j = i + 1; j < n; j++) {
-                    int v = Ji[j];
-                    row += ((c >> j) & 1ull) ? v : -v;
+                    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+                    if ((tid & 31) == 0) s_ER[tid >> 5] = part;
+                } else if (tid < kMaxN + kVarBits) {
+                    const int b = tid - kMaxN;
+                    if (b < nv) s_fR[b] = field_at(s, n, walk_shift + b, cR);
+                } else if (tid < kMaxN + kVarBits + IB) {
+                    const int k = tid - kMaxN - kVarBits;
+                    int f = s.hq[k];
+                    const int* Jk = s.Jq + k * n;
+                    for (int j = IB; j < n; j++) {
+                        const int v = Jk[j];
+                        f += ((cR >> j) & 1ull) ? v : -v;
+                    }
+                    s_gR[k] = f;
+                } else if (tid < kMaxN + kVarBits + IB + kKeep) {
+                    const int r = tid - kMaxN - kVarBits - IB;
+                    s_fmR[r] = field_at(s, n, IB + r, cR);
                 }
-                e += ((c >> i) & 1ull) ? row : -row;
             }
-            E0[w] = e;
+            __syncthreads();
+
+            // flips of the task bits 2..nv-1 that the thread's walks share (unsigned
+            // arithmetic: exact modulo 2^32, and every true result fits in int32)
+            const unsigned xt = (unsigned)tid * kWalks;
+            const unsigned vmask = (1u << nv) - 1u;
+            unsigned Et = 0u, P0 = 0u, P1 = 0u;
+            unsigned Gt[IB], Ft[kKeep];
 #pragma unroll
-            for (int k = 0; k < IB; k++) {
-                int f = s.hq[k];
-                const int* Jk = s.Jq + k * n;
-                for (int j = IB; j < n; j++) {
-                    int v = Jk[j];
-                    f += ((c >> j) & 1ull) ? v : -v;
+            for (int k = 0; k < IB; k++) Gt[k] = 0u;
+#pragma unroll
+            for (int r = 0; r < kKeep; r++) Ft[r] = 0u;
+            for (int b = 2; b < nv; b++) {
+                const unsigned on = 0u - ((xt >> b) & 1u);
+                const int v = walk_shift + b;
+                const int* Jv = s.Jq + v * n + walk_shift;
+                unsigned pair = 0u;
+                for (int b2 = 2; b2 < b; b2++) pair += (unsigned)Jv[b2] & (0u - ((xt >> b2) & 1u));
+                Et += ((unsigned)s_fR[b] * 2u + pair * 4u) & on;
+                P0 += (unsigned)Jv[0] & on;
+                P1 += (unsigned)Jv[1] & on;
+                int colv[16];
+#pragma unroll
+                for (int q4 = 0; q4 < 4; q4++) {
+                    const int4 cv = *reinterpret_cast<const int4*>(&s.col[v][4 * q4]);
+                    colv[4 * q4 + 0] = cv.x;
+                    colv[4 * q4 + 1] = cv.y;
+                    colv[4 * q4 + 2] = cv.z;
+                    colv[4 * q4 + 3] = cv.w;
                 }
-                G[w][k] = 2 * f;
+#pragma unroll
+                for (int k = 0; k < IB; k++) Gt[k] += ((unsigned)colv[k] * 4u) & on;
+#pragma unroll
+                for (int r = 0; r < kKeep; r++) Ft[r] += ((unsigned)colv[IB + r] * 2u) & on;
+            }
+            const unsigned ER = (unsigned)s_ER[0] + (unsigned)s_ER[1];
+
+#pragma unroll
+            for (int w = 0; w < kWalks; w++) {
+                // an inactive walk (task >= ntasks) keeps a valid configuration; its hits are ignored
+                active[w] = base + (unsigned long long)(xt + w) < p.ntasks;
+                unsigned e = ER + Et;
+                unsigned g[IB], fm[kKeep];
+#pragma unroll
+                for (int k = 0; k < IB; k++) g[k] = (unsigned)s_gR[k] * 2u + Gt[k];
+#pragma unroll
+                for (int r = 0; r < kKeep; r++) fm[r] = (unsigned)s_fmR[r] + Ft[r];
+                unsigned long long c = cR | ((unsigned long long)(xt & vmask) << walk_shift);
+#pragma unroll
+                for (int b = 0; b < 2; b++) {
+                    if (!((w >> b) & 1) || b >= nv) continue;
+                    const int v = walk_shift + b;
+                    unsigned d = (unsigned)s_fR[b] * 2u + (b == 0 ? P0 : P1) * 4u;
+                    if (b == 1 && (w & 1)) d += (unsigned)s.Jq[v * n + walk_shift] * 4u;
+                    e += d;
+#pragma unroll
+                    for (int k = 0; k < IB; k++) g[k] += (unsigned)s.col[v][k] * 4u;
+#pragma unroll
+                    for (int r = 0; r < kKeep; r++) fm[r] += (unsigned)s.col[v][IB + r] * 2u;
+                    c |= 1ull << v;
+                }
+                E0[w] = (int)e;
+#pragma unroll
+                for (int k = 0; k < IB; k++) G[w][k] = (int)g[k];
+#pragma unroll
+                for (int r = 0; r < kKeep; r++) Fm[w][r] = (int)fm[r];
+                cfg0[w] = c;
+            }
+
+        } else {
+            // long tasks (>= 2^13 blocks each): each walk evaluates its start directly
+#pragma unroll
+            for (int w = 0; w < kWalks; w++) {
+                unsigned long long task = base + (unsigned long long)(tid * kWalks + w);
+                active[w] = task < p.ntasks;
+                if (!active[w]) task = 0;   // a valid walk whose hits are ignored
+                cfg0[w] = p.hiconst | (task << walk_shift);
             }
 #pragma unroll
-            for (int r = 0; r < kKeep; r++) Fm[w][r] = field_at(s, n, IB + r, c);
+            for (int w = 0; w < kWalks; w++) {
+                const unsigned long long c = cfg0[w];
+                int e = 0;
+                for (int i = 0; i < n; i++) {
+                    int row = s.hq[i];
+                    const int* Ji = s.Jq + i * n;
+                    for (int j = i + 1; j < n; j++) {
+                        int v = Ji[j];
+                        row += ((c >> j) & 1ull) ? v : -v;
+                    }
+                    e += ((c >> i) & 1ull) ? row : -row;
+                }
+                E0[w] = e;
+#pragma unroll
+                for (int k = 0; k < IB; k++) {
+                    int f = s.hq[k];
+                    const int* Jk = s.Jq + k * n;
+                    for (int j = IB; j < n; j++) {
+                        int v = Jk[j];
+                        f += ((c >> j) & 1ull) ? v : -v;
+                    }
+                    G[w][k] = 2 * f;
+                }
+#pragma unroll
+                for (int r = 0; r < kKeep; r++) Fm[w][r] = field_at(s, n, IB + r, c);
+            }
+
         }
 
         Packed<IB> pk;
@@ -237,21 +390,24 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
             inner_walk<IB>(pk, p, std::make_integer_sequence<int, IS - 1>{});
             const bool flag_lo = (pk.M & 0xffffu) <= thr16;
             const bool flag_hi = (pk.M >> 16) <= thr16;
-            if (flag_lo || flag_hi) {
+            if (__any_sync(0xffffffffu, flag_lo || flag_hi)) {
+                // the warp rescans its flagged walks one at a time, all lanes on each
 #pragma unroll
                 for (int w = 0; w < kWalks; w++) {
-                    const bool lane_hi = (w & 1) != 0;
-                    if (!active[w] || !(lane_hi ? flag_hi : flag_lo)) continue;
-                    const unsigned ebase = (unsigned)E0[w] - (unsigned)s.T[0];
-                    const unsigned long long cb = cfg0[w] | cmid;
-                    for (int t = 0; t < IS; t++) {
-                        const int g = t ^ (t >> 1);
-                        unsigned acc = ebase + (unsigned)s.T[g];
+                    unsigned todo = __ballot_sync(0xffffffffu, active[w] && ((w & 1) ? flag_hi : flag_lo));
+                    while (todo) {
+                        const int src = __ffs(todo) - 1;
+                        todo &= todo - 1u;
+                        if (lane == src) {
 #pragma unroll
-                        for (int k = 0; k < IB; k++) acc += ((g >> k) & 1) ? (unsigned)G[w][k] : 0u;
-                        const int e = (int)acc;   // E(g) = E0 + sum_{k in g} G_k + T[g] - T[0]
-                        const unsigned long long c = cb | (unsigned long long)g;
-                        if (e <= tau_scr && !(e == tie_E && c > tie_C)) record(p, s, &s_buf_count, e, c);
+                            for (int k = 0; k < IB; k++) s_Gw[warp][k] = G[w][k];
+                        }
+                        __syncwarp();
+                        const unsigned e0 = (unsigned)__shfl_sync(0xffffffffu, E0[w], src);
+                        const unsigned long long cb = __shfl_sync(0xffffffffu, cfg0[w], src) | cmid;
+                        warp_rescan<IB>(p, s, &s_buf_count, e0 - (unsigned)s.T[0], s_Gw[warp], cb, tau_scr, tie_E,
+                                        tie_C, lane);
+                        __syncwarp();
                     }
                 }
             }

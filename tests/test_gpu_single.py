@@ -150,6 +150,24 @@ def test_n64_subspace(bf, o):
     check(bf, o, Ji, hi, 20, fixed_bits=45, fixed_value=987654321)
 
 
+def test_local_search_seed_union_of_balls(bf, o):
+    """n = 26, S = 1500 > 1 + 26 + 325: the sampled seed runs first and the union of the
+    Hamming balls around several local minima may only lower its threshold."""
+    J, h = rand_float(26, 261)
+    check(bf, o, J, h, 1500)
+    Ji, hi = rand_pm1(26, 262)
+    check(bf, o, Ji, hi, 1500)
+
+
+def test_local_search_seed_in_subspace(bf, o):
+    """The local search flips free spins only: n = 44 with the top 20 bits fixed
+    (2^24 configurations, local-search seed alone)."""
+    Ji, hi = rand_pm1(44, 440)
+    check(bf, o, Ji, hi, 200, fixed_bits=20, fixed_value=0xABCDE)
+    J, h = rand_float(44, 441)
+    check(bf, o, J, h, 100, fixed_bits=20, fixed_value=0x12345)
+
+
 def test_task_and_grid_options(bf, o):
     J, h = rand_float(22, 41)
     ref = None
