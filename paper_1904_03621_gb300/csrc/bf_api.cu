@@ -31,6 +31,40 @@ struct ProfileEvents {
 };
 thread_local ProfileEvents g_prof;
 
+// Host copies of prep results that wait only for the work queued on the caller's stream
+// before side_mark(): the copy runs on a per-thread side stream behind an event, so the seed
+// kernels queued on the caller's stream in between keep the GPU busy while the host waits.
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev = nullptr;
+};
+constexpr int kMaxDevices = 64;
+thread_local SideStream g_side[kMaxDevices];
+
+cudaError_t side_mark(cudaStream_t stream, SideStream*& ss)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    ss = &g_side[dev];
+    if (!ss->s) {
+        e = cudaStreamCreateWithFlags(&ss->s, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+        e = cudaEventCreateWithFlags(&ss->ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaEventRecord(ss->ev, stream);
+}
+
+cudaError_t side_copy(void* dst, const void* src, size_t bytes, SideStream* ss)
+{
+    cudaError_t e = cudaStreamWaitEvent(ss->s, ss->ev, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, ss->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ss->s);
+    return e;
+}
+
 bf_status fail(bf_status s, const char* fmt, ...)
 {
     char buf[512];
@@ -258,14 +292,9 @@ bf_status bf_low_spectrum(const void* J, const void* h, int n, int S, bf_dtype d
     cudaError_t e = bf::launch_prep(pp, stream);
     if (e != cudaSuccess) return cuda_fail(e, "prep kernel");
 
-    // The per-instance increments of the unrolled walk become kernel
-    // parameters (constant bank operands of the inner loop).
-    bf::PrepLaunch hl;
-    e = cudaMemcpyAsync(&hl, &prep->L, sizeof(hl), cudaMemcpyDeviceToHost, stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-    if (e != cudaSuccess) return cuda_fail(e, "prep copy");
-    if (hl.status & bf::kErrRange)
-        return fail(BF_EUNSUPPORTED, "couplings outside the int32 fixed-point range (sum|J|+sum|h| = %g)", hl.emax);
+    SideStream* side = nullptr;
+    e = side_mark(stream, side);
+    if (e != cudaSuccess) return cuda_fail(e, "prep event");
 
     int* AE = reinterpret_cast<int*>(ws + L.listA_E);
     auto* AC = reinterpret_cast<unsigned long long*>(ws + L.listA_C);
@@ -291,6 +320,14 @@ bf_status bf_low_spectrum(const void* J, const void* h, int n, int S, bf_dtype d
                                     reinterpret_cast<unsigned long long*>(ws + L.best_C), ball_only, hdr, stream);
         if (e != cudaSuccess) return cuda_fail(e, "local-search seed");
     }
+
+    // The per-instance increments of the unrolled walk become kernel
+    // parameters (constant bank operands of the inner loop); the seed runs meanwhile.
+    bf::PrepLaunch hl;
+    e = side_copy(&hl, &prep->L, sizeof(hl), side);
+    if (e != cudaSuccess) return cuda_fail(e, "prep copy");
+    if (hl.status & bf::kErrRange)
+        return fail(BF_EUNSUPPORTED, "couplings outside the int32 fixed-point range (sum|J|+sum|h| = %g)", hl.emax);
 
     bf::GrayParams gp{};
     std::memcpy(gp.dT16, hl.dT16, sizeof(gp.dT16));
@@ -535,10 +572,9 @@ bf_status bf_low_spectrum_potts(const void* J, const void* h, int n, int q, int 
     struct { int q, status, qs, W; double delta, emax; int dT[bf::kPottsMaxSteps]; unsigned dT16[bf::kPottsMaxSteps]; } hp;
     static_assert(offsetof(bf::PottsPrep, dT) == 32, "PottsPrep header layout");
     static_assert(offsetof(bf::PottsPrep, dT16) == 32 + 4 * bf::kPottsMaxSteps, "PottsPrep header layout");
-    e = cudaMemcpyAsync(&hp, prep, sizeof(hp), cudaMemcpyDeviceToHost, stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-    if (e != cudaSuccess) return cuda_fail(e, "Potts prep copy");
-    if (hp.status & bf::kErrRange) return fail(BF_EUNSUPPORTED, "instance outside the fixed-point range");
+    SideStream* side = nullptr;
+    e = side_mark(stream, side);
+    if (e != cudaSuccess) return cuda_fail(e, "Potts prep event");
 
     int* AE = reinterpret_cast<int*>(ws + L.listA_E);
     auto* AC = reinterpret_cast<unsigned long long*>(ws + L.listA_C);
@@ -552,6 +588,11 @@ bf_status bf_low_spectrum_potts(const void* J, const void* h, int n, int q, int 
     if (e != cudaSuccess) return cuda_fail(e, "Potts seed merge");
     e = bf::launch_set_tau(in_a ? AE : BE, S, hdr, stream);
     if (e != cudaSuccess) return cuda_fail(e, "Potts seed threshold");
+
+    // the seed runs while the host waits for the per-instance walk constants
+    e = side_copy(&hp, prep, sizeof(hp), side);
+    if (e != cudaSuccess) return cuda_fail(e, "Potts prep copy");
+    if (hp.status & bf::kErrRange) return fail(BF_EUNSUPPORTED, "instance outside the fixed-point range");
 
     bf::PottsParams pp{};
     std::memcpy(pp.dT, hp.dT, sizeof(pp.dT));

@@ -243,6 +243,8 @@ struct PottsSmem {
     int* Ct;                  // [walk][m*Q][threads]: exact C_p(v) of each walk's middle digits
     int* E;                   // 2*cap
     unsigned long long* C;    // 2*cap
+    int* step;                // q^B: Gray step t changes table entry step[t] >> 1, upward if step[t] & 1
+    int* xin;                 // q^B: inner configuration sum_k d_k q^k after step t
 };
 
 // integer packing hi * 2^16 + lo of two signed 16-bit increments
@@ -295,13 +297,74 @@ __device__ __forceinline__ void potts_record(const PottsParams& p, const PottsSm
     }
 }
 
+// 32-bit forms of the q-adic valuation and the reflected Gray digit for the block counter of
+// the middle digits (q^m <= 256 blocks per task): division by the constant Q stays cheap.
+template <int Q>
+__device__ __forceinline__ int qval32(unsigned t)
+{
+    int k = 0;
+    while (t % Q == 0u) { t /= Q; k++; }
+    return k;
+}
+
+template <int Q>
+__device__ __forceinline__ int gray_digit32(unsigned u, int pos)
+{
+    for (int i = 0; i < pos; i++) u /= Q;
+    const int d = (int)(u % Q);
+    return ((u / Q) & 1u) ? Q - 1 - d : d;
+}
+
+// Exact rescan of one walk's block by a whole warp.  Lane L takes the R = ceil(q^B / 32)
+// Gray steps t = L*R .. L*R + R - 1.  It evaluates its first configuration directly:
+//   E = Ebase + sum_k (f_k(d_k) - f_k(0)) - sum_{k<l<B} J_kl [d_k != d_l]
+// (Ebase has all inner digits 0, so every inner pair is equal there), then follows the
+// steps as the walk does: +-G_k(v) for the changed digit plus the pair-table difference.
+// G points at the walk's field table G_k(v) = f_k(v+1) - f_k(v), entry e at G[e * threads].
+template <int Q, int B>
+__device__ __forceinline__ void potts_warp_rescan(const PottsParams& p, const PottsSmem& s, unsigned* buf_count,
+                                                  unsigned ebase, const int* G, unsigned long long cb, int tau,
+                                                  int tie_E, unsigned long long tie_C, int n, int lane)
+{
+    constexpr int P = (int)potts_pow(Q, B);
+    constexpr int R = (P + 31) / 32;
+    const int t0 = lane * R;
+    if (t0 >= P) return;
+    const int t1 = t0 + R < P ? t0 + R : P;
+    int d[B];
+    int x = s.xin[t0];
+#pragma unroll
+    for (int k = 0; k < B; k++) {
+        d[k] = x % Q;
+        x /= Q;
+    }
+    unsigned e = ebase;
+#pragma unroll
+    for (int k = 0; k < B; k++) {
+        for (int v = 0; v < d[k]; v++) e += (unsigned)G[(k * (Q - 1) + v) * kPottsThreads];
+#pragma unroll
+        for (int l = k + 1; l < B; l++)
+            if (d[k] != d[l]) e -= (unsigned)s.Jq[k * n + l];
+    }
+    for (int t = t0; t < t1; t++) {
+        if (t > t0) {
+            const int st = s.step[t];
+            const unsigned g = (unsigned)G[(st >> 1) * kPottsThreads];
+            e += ((st & 1) ? g : 0u - g) + (unsigned)p.dT[t];
+        }
+        const int ei = (int)e;
+        const unsigned long long c = cb + (unsigned long long)s.xin[t];
+        if (ei <= tau && !(ei == tie_E && c > tie_C)) potts_record(p, s, buf_count, ei, c);
+    }
+}
+
 // Each thread walks two tasks at once: their 16-bit energy views share one register, so one
 // IADD3 advances both and one 3-input 16x2 minimum folds two steps.  A digit's increment is
 // the difference of the floors of its cumulative field offset F_k(v) = f_k(v) - f_k(0), so the
 // views telescope exactly and, as for the Ising walk,
 //     E/2^16 - (B + 2) < x - 2^15 <= E/2^16 + 1 ,
 // and x <= floor((tau + 2^31) / 2^16) + 1 catches every E <= tau.  Flagged walks are
-// rescanned exactly from their int32 tables.
+// rescanned exactly from their int32 tables, by the whole warp.
 template <int Q>
 __global__ void __launch_bounds__(kPottsThreads, 2) potts_walk_kernel(const __grid_constant__ PottsParams p)
 {
@@ -319,6 +382,8 @@ __global__ void __launch_bounds__(kPottsThreads, 2) potts_walk_kernel(const __gr
     s.Ct = s.Gt + NW * NG * kPottsThreads;
     s.Jq = s.Ct + NW * kPottsMidTable * kPottsThreads;
     s.hq = s.Jq + n * n;
+    s.step = s.hq + n * Q;
+    s.xin = s.step + P;
 
     __shared__ unsigned s_buf_count;
     __shared__ int s_list_count, s_kE;
@@ -328,6 +393,19 @@ __global__ void __launch_bounds__(kPottsThreads, 2) potts_walk_kernel(const __gr
     const PottsPrep* prep = p.prep;
     for (int i = tid; i < n * n; i += blockDim.x) s.Jq[i] = prep->Jq[i];
     for (int i = tid; i < n * Q; i += blockDim.x) s.hq[i] = prep->hq[i];
+    for (int t = tid; t < P; t += blockDim.x) {
+        int x = 0, qk = 1;
+        for (int k = 0; k < B; k++, qk *= Q) x += potts_gray_digit((unsigned long long)t, Q, k) * qk;
+        s.xin[t] = x;
+        int st = 0;
+        if (t > 0) {
+            const int k = potts_qval((unsigned long long)t, Q);
+            const int a0 = potts_gray_digit((unsigned long long)(t - 1), Q, k);
+            const int a1 = potts_gray_digit((unsigned long long)t, Q, k);
+            st = ((k * (Q - 1) + (a1 > a0 ? a0 : a1)) << 1) | (a1 > a0 ? 1 : 0);
+        }
+        s.step[t] = st;
+    }
     if (tid == 0) {
         s_buf_count = 0u;
         s_list_count = 0;
@@ -443,29 +521,25 @@ __global__ void __launch_bounds__(kPottsThreads, 2) potts_walk_kernel(const __gr
             potts_block<Q, B>(X, X1, M, G, p, std::make_integer_sequence<int, P - 1>{});
             M = __vminu2(M, X1);
             const bool flag[NW] = {active[0] && (M & 0xffffu) <= thr16, active[1] && (M >> 16) <= thr16};
-#pragma unroll 1
-            for (int w = 0; w < NW; w++) {
-                if (!flag[w]) continue;
-                // exact rescan of walk w's block
+            if (__any_sync(0xffffffffu, flag[0] || flag[1])) {
                 unsigned long long mid = 0ull;
-                for (int pm = 0; pm < m; pm++) mid += (unsigned long long)potts_gray_digit(u, Q, pm) * p.qpow[pm];
-                const unsigned long long cb = c0[w] + mid * p.qpow[B];
-                unsigned e = Ebase[w];
-                unsigned long long x = 0ull;
-                for (int t = 0; t < P; t++) {
-                    if (t > 0) {
-                        const int k = potts_qval((unsigned long long)t, Q);
-                        const int a0 = potts_gray_digit((unsigned long long)(t - 1), Q, k);
-                        const int a1 = potts_gray_digit((unsigned long long)t, Q, k);
-                        const bool up = a1 > a0;
-                        const unsigned g = (unsigned)Gt[(w * NG + k * (Q - 1) + (up ? a0 : a1)) * kPottsThreads];
-                        e += (up ? g : 0u - g) + (unsigned)p.dT[t];
-                        x = up ? x + p.qpow[k] : x - p.qpow[k];
+                for (int pm = 0; pm < m; pm++) mid += (unsigned long long)gray_digit32<Q>((unsigned)u, pm) * p.qpow[pm];
+                const unsigned long long midc = mid * p.qpow[B];
+                const int lane = tid & 31;
+#pragma unroll
+                for (int w = 0; w < NW; w++) {
+                    unsigned todo = __ballot_sync(0xffffffffu, flag[w]);
+                    while (todo) {
+                        const int src = __ffs(todo) - 1;
+                        todo &= todo - 1u;
+                        const unsigned eb = __shfl_sync(0xffffffffu, Ebase[w], src);
+                        const unsigned long long cw = __shfl_sync(0xffffffffu, c0[w], src);
+                        const int* Gs = s.Gt + (tid - lane + src) + w * NG * kPottsThreads;
+                        potts_warp_rescan<Q, B>(p, s, &s_buf_count, eb, Gs, cw + midc, tau_scr, tie_E, tie_C, n,
+                                                lane);
                     }
-                    const int ei = (int)e;
-                    const unsigned long long c = cb + x;
-                    if (ei <= tau_scr && !(ei == tie_E && c > tie_C)) potts_record(p, s, &s_buf_count, ei, c);
                 }
+                __syncwarp();   // the tables of other lanes were read: they change below
             }
 
             // ---- segment boundary: merge the buffer into the block list
@@ -511,8 +585,8 @@ __global__ void __launch_bounds__(kPottsThreads, 2) potts_walk_kernel(const __gr
 
             // ---- change one middle digit: pm = q-adic valuation of u + 1, a -> a2 (both walks)
             if (u + 1 < nblocks) {
-                const int pm = potts_qval(u + 1, Q);
-                const int a = potts_gray_digit(u, Q, pm), a2 = potts_gray_digit(u + 1, Q, pm);
+                const int pm = qval32<Q>((unsigned)u + 1u);
+                const int a = gray_digit32<Q>((unsigned)u, pm), a2 = gray_digit32<Q>((unsigned)u + 1u, pm);
                 const int sp = B + pm;
 #pragma unroll
                 for (int w = 0; w < NW; w++) {
@@ -550,7 +624,8 @@ size_t potts_walk_smem(int q, int n, int list_cap)
 {
     const int B = potts_inner_digits(q);
     return (size_t)2 * list_cap * 12 + (size_t)kPottsWalks * B * (q - 1) * kPottsThreads * 4 +
-           (size_t)kPottsWalks * kPottsMidTable * kPottsThreads * 4 + (size_t)n * n * 4 + (size_t)n * q * 4;
+           (size_t)kPottsWalks * kPottsMidTable * kPottsThreads * 4 + (size_t)n * n * 4 + (size_t)n * q * 4 +
+           (size_t)potts_pow(q, B) * 8;
 }
 
 template <int Q>
