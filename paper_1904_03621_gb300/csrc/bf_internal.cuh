@@ -89,6 +89,16 @@ __host__ __device__ inline bool rec_less(int ea, unsigned long long ca, int eb, 
     return ea < eb || (ea == eb && ca < cb);
 }
 
+// splitmix64 finaliser (Steele, Lea, Flood 2014): a bijective 64-bit mix, used to spread
+// pseudo-random starting configurations
+__host__ __device__ inline unsigned long long splitmix64(unsigned long long x)
+{
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
 constexpr int kEmptyE = 0x7fffffff;
 constexpr unsigned long long kEmptyC = ~0ull;
 

@@ -37,6 +37,8 @@ constexpr int kBUnitWalkBits = 10;            // a work unit: 2^10 walks (256 th
 constexpr int kBBuf = 2 * kInnerSteps;       // records per warp buffer (room for one walk's rescan)
 constexpr int kBSeed = 1024;                  // sampled configurations per instance for its first threshold
 constexpr int kBSeedThreads = 256;
+constexpr int kBDescents = 2;                 // local searches per warp of the preparation block
+constexpr unsigned long long kBDescentSalt = 0x13198A2E03707344ull;
 constexpr size_t kBWarpSmem = (size_t)kBBuf * 12;                 // record buffer bytes per warp
 constexpr int kBSyncEvery = 1;                   // unrolled blocks between block barriers
 // + the unit's tables: dT16, T (kInnerSteps each), J_q (kBMaxN^2), h_q (kBMaxN), columns (kBMaxN x 16)
@@ -130,7 +132,8 @@ __global__ void __launch_bounds__(kBSeedThreads, 2) bprep_kernel(const BatchPara
     __shared__ __align__(16) int dTx[kInnerSteps];   // exact T[gray(t)] - T[gray(t-1)]
     __shared__ int sE[kBSeed];
     __shared__ unsigned long long sC[kBSeed];
-    __shared__ int s_q, s_status;
+    __shared__ int s_q, s_status, s_tau, s_dE[kBSeedThreads / 32], s_F[kBMaxN];
+    __shared__ unsigned long long s_dC[kBSeedThreads / 32];
     __shared__ double s_emax;
 
     const int b = blockIdx.x, tid = threadIdx.x;
@@ -218,6 +221,7 @@ __global__ void __launch_bounds__(kBSeedThreads, 2) bprep_kernel(const BatchPara
     // decomposition E(g) = E0 + sum_{k in g} G_k + T[g] - T[0] over the 9 inner spins, twice
     // (spin 9 at -1, then at +1), one add per configuration.
     // Smaller n: exact energies of a pseudo-random sample of 1024 (all if fewer).
+    // A local search below may lower the bound.
     const unsigned long long space = 1ull << n;
     if (n >= 18) {
         const unsigned long long hi_mask = (space >> 10) - 1ull;
@@ -269,6 +273,95 @@ __global__ void __launch_bounds__(kBSeedThreads, 2) bprep_kernel(const BatchPara
         }
     }
     block_sort(sE, sC, kBSeed);
+    if (tid == 0) s_tau = sE[p.S - 1];
+
+    // A second bound from a local search (n > 10; smaller spaces were enumerated above):
+    // each warp runs steepest-descent searches from pseudo-random starts, lane l holding the
+    // local field of spin l (flipping spin i changes Eq. (1) by -2 s_i f_i).  The S-th
+    // lowest energy of the 1 + n + n(n-1)/2 distinct configurations within Hamming distance 2
+    // of the best minimum bounds the S-th energy too; the lower of the two bounds is kept.
+    const int ball = 1 + n + n * (n - 1) / 2;
+    if (n > 10 && ball >= p.S) {
+        const int lane = tid & 31, warp = tid >> 5;
+        int bE = kEmptyE;
+        unsigned long long bC = kEmptyC;
+        for (int r = 0; r < kBDescents; r++) {
+            const unsigned long long id = ((unsigned long long)b * (kBSeedThreads / 32) + warp) * kBDescents + r;
+            unsigned long long c = splitmix64(kBDescentSalt + id) & (space - 1ull);
+            unsigned f = 0u;
+            if (lane < n) {
+                f = (unsigned)hq[lane];
+                for (int j = 0; j < n; j++) {
+                    const unsigned v = (unsigned)Jq[j * n + lane];
+                    f += ((c >> j) & 1ull) ? v : 0u - v;
+                }
+            }
+            unsigned t2 = 0u;
+            if (lane < n) {
+                const unsigned fh = f + (unsigned)hq[lane];
+                t2 = ((c >> lane) & 1ull) ? fh : 0u - fh;
+            }
+            int E = (int)__reduce_add_sync(0xffffffffu, t2) >> 1;   // 2E = sum_i s_i (f_i + h_i)
+            for (int it = 0; it < 4 * n; it++) {
+                const int v = lane < n ? (((c >> lane) & 1ull) ? (int)f : -(int)f) : INT_MIN;
+                const int best = __reduce_max_sync(0xffffffffu, v);
+                if (best <= 0) break;
+                const int k = __ffs(__ballot_sync(0xffffffffu, v == best)) - 1;
+                c ^= 1ull << k;
+                E -= 2 * best;
+                if (lane < n) {
+                    const unsigned d = (unsigned)Jq[k * n + lane] << 1;
+                    f += ((c >> k) & 1ull) ? d : 0u - d;
+                }
+            }
+            if (rec_less(E, c, bE, bC)) { bE = E; bC = c; }
+        }
+        if (lane == 0) { s_dE[warp] = bE; s_dC[warp] = bC; }
+        __syncthreads();
+        if (tid == 0) {
+            for (int w2 = 1; w2 < kBSeedThreads / 32; w2++)
+                if (rec_less(s_dE[w2], s_dC[w2], s_dE[0], s_dC[0])) { s_dE[0] = s_dE[w2]; s_dC[0] = s_dC[w2]; }
+        }
+        __syncthreads();
+        const unsigned long long c0 = s_dC[0];
+        const int E0 = s_dE[0];
+        if (tid < n) {
+            unsigned f = (unsigned)hq[tid];
+            for (int j = 0; j < n; j++) {
+                const unsigned v = (unsigned)Jq[j * n + tid];
+                f += ((c0 >> j) & 1ull) ? v : 0u - v;
+            }
+            s_F[tid] = (int)f;
+        }
+        __syncthreads();
+        // slot x: 0 = the minimum, 1..n single flips, then the pairs i < j in row order
+        for (int x = tid; x < kBSeed; x += blockDim.x) {
+            if (x >= ball) { sE[x] = kEmptyE; sC[x] = kEmptyC; continue; }
+            unsigned e = (unsigned)E0;
+            unsigned long long cx = c0;
+            if (x >= 1 && x <= n) {
+                const int i = x - 1;
+                const unsigned sf = ((c0 >> i) & 1ull) ? (unsigned)s_F[i] : 0u - (unsigned)s_F[i];
+                e -= sf << 1;
+                cx ^= 1ull << i;
+            } else if (x > n) {
+                int pr = x - 1 - n, i = 0;
+                while (pr >= n - 1 - i) { pr -= n - 1 - i; i++; }
+                const int j = i + 1 + pr;
+                const bool si = (c0 >> i) & 1ull, sj = (c0 >> j) & 1ull;
+                const unsigned fi = si ? (unsigned)s_F[i] : 0u - (unsigned)s_F[i];
+                const unsigned fj = sj ? (unsigned)s_F[j] : 0u - (unsigned)s_F[j];
+                const unsigned jij = (unsigned)Jq[i * n + j] << 2;
+                e = e - (fi << 1) - (fj << 1) + (si == sj ? jij : 0u - jij);
+                cx ^= (1ull << i) | (1ull << j);
+            }
+            sE[x] = (int)e;
+            sC[x] = cx;
+        }
+        block_sort(sE, sC, kBSeed);
+        if (tid == 0 && sE[p.S - 1] < s_tau) s_tau = sE[p.S - 1];
+    }
+    __syncthreads();
     // outputs
     for (int idx = tid; idx < n * n; idx += blockDim.x) I->Jq[idx] = Jq[idx];
     for (int i = tid; i < kBMaxN; i += blockDim.x) I->hq[i] = i < n ? hq[i] : 0;
@@ -307,7 +400,7 @@ __global__ void __launch_bounds__(kBSeedThreads, 2) bprep_kernel(const BatchPara
         I->units = nh > kBUnitWalkBits ? (1ull << (nh - kBUnitWalkBits)) : 1ull;
         I->delta = delta;
         I->emax = s_emax;
-        p.tau[b] = sE[p.S - 1];
+        p.tau[b] = s_tau;
         p.pool_count[b] = 0u;
         if (status) atomicOr(&p.hdr->status, (unsigned)status);
     }

@@ -42,15 +42,6 @@ constexpr int kBallMax = 4096;        // records of the union of balls (one ball
 constexpr int kBallCenters = 8;       // distinct minima whose balls are evaluated
 constexpr unsigned long long kDescentSalt = 0x243F6A8885A308D3ull;
 
-// splitmix64 finaliser (Steele, Lea, Flood 2014): a bijective 64-bit mix
-__device__ __forceinline__ unsigned long long mix64(unsigned long long x)
-{
-    x += 0x9E3779B97F4A7C15ull;
-    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
-    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
-    return x ^ (x >> 31);
-}
-
 // lowest (E, c) of the 32 lanes' records, returned to every lane
 __device__ __forceinline__ void warp_min_record(int& e, unsigned long long& c)
 {
@@ -84,7 +75,7 @@ __global__ void __launch_bounds__(kDescentThreads) descent_kernel(const Prep* pr
     unsigned long long bC = kEmptyC;
     for (int r = 0; r < kDescentRounds; r++) {
         const unsigned long long id = ((unsigned long long)blockIdx.x * (kDescentThreads / 32) + warp) * kDescentRounds + r;
-        unsigned long long c = hiconst | (mix64(kDescentSalt + id) & mask);
+        unsigned long long c = hiconst | (splitmix64(kDescentSalt + id) & mask);
         // local fields f_i = h_i + sum_j J_ji s_j (exact modulo 2^32, true values below 2^29)
         unsigned f0 = (unsigned)h0, f1 = (unsigned)h1;
         for (int j = 0; j < n; j++) {
