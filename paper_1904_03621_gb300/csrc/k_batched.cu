@@ -272,7 +272,13 @@ __global__ void __launch_bounds__(kBSeedThreads, 2) bprep_kernel(const BatchPara
             sC[x] = c;
         }
     }
-    block_sort(sE, sC, kBSeed);
+    // the seed filled 256 minima (n >= 18) or min(2^n, kBSeed) samples; the rest is empty
+    {
+        const int filled = n >= 18 ? kBSeedThreads : (space < (unsigned long long)kBSeed ? (int)space : kBSeed);
+        int len = 2;
+        while (len < filled || len < p.S) len <<= 1;
+        block_sort(sE, sC, len);
+    }
     if (tid == 0) s_tau = sE[p.S - 1];
 
     // A second bound from a local search (n > 10; smaller spaces were enumerated above):
@@ -335,7 +341,9 @@ __global__ void __launch_bounds__(kBSeedThreads, 2) bprep_kernel(const BatchPara
         }
         __syncthreads();
         // slot x: 0 = the minimum, 1..n single flips, then the pairs i < j in row order
-        for (int x = tid; x < kBSeed; x += blockDim.x) {
+        int blen = 2;
+        while (blen < ball) blen <<= 1;
+        for (int x = tid; x < blen; x += blockDim.x) {
             if (x >= ball) { sE[x] = kEmptyE; sC[x] = kEmptyC; continue; }
             unsigned e = (unsigned)E0;
             unsigned long long cx = c0;
@@ -358,7 +366,7 @@ __global__ void __launch_bounds__(kBSeedThreads, 2) bprep_kernel(const BatchPara
             sE[x] = (int)e;
             sC[x] = cx;
         }
-        block_sort(sE, sC, kBSeed);
+        block_sort(sE, sC, blen);
         if (tid == 0 && sE[p.S - 1] < s_tau) s_tau = sE[p.S - 1];
     }
     __syncthreads();
@@ -854,18 +862,22 @@ __global__ void __launch_bounds__(kBFinalThreads) bfinal_kernel(const BatchParam
     if (I->status & kErrArg) return;
     unsigned cnt = *(volatile unsigned*)&p.pool_count[b];
     if (cnt > (unsigned)p.pool_cap) cnt = p.pool_cap;
-    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+    // sort only the filled part of the pool (a power of two >= max(cnt, S))
+    int lenb = 2;
+    while (lenb < (int)cnt || lenb < S) lenb <<= 1;
+    if (lenb > len) lenb = len;
+    for (int i = threadIdx.x; i < lenb; i += blockDim.x) {
         bool ok = i < (int)cnt;
         E[i] = ok ? p.pool_E[(size_t)b * p.pool_cap + i] : kEmptyE;
         C[i] = ok ? p.pool_C[(size_t)b * p.pool_cap + i] : kEmptyC;
     }
-    block_sort(E, C, len);
+    block_sort(E, C, lenb);
     if (threadIdx.x == 0) {
-        int valid = upper_bound_key(E, len, INT_MAX - 1);
+        int valid = upper_bound_key(E, lenb, INT_MAX - 1);
         int keep = valid < S ? valid : S;
         if (valid >= S && I->W > 0) {
             long long lim = (long long)E[S - 1] + I->W;
-            keep = upper_bound_key(E, len, lim > INT_MAX - 1 ? INT_MAX - 1 : (int)lim);
+            keep = upper_bound_key(E, lenb, lim > INT_MAX - 1 ? INT_MAX - 1 : (int)lim);
         }
         if (valid < S) atomicOr(&p.hdr->status, kErrSpill);   // cannot happen unless records were lost
         s_keep = keep;
@@ -883,7 +895,10 @@ __global__ void __launch_bounds__(kBFinalThreads) bfinal_kernel(const BatchParam
     // FP64 re-evaluation of Eq. (1) for the kept records, then reselection by (E, c)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const long long jo = p.J_off[b], ho = p.h_off[b];
-    for (int r = warp; r < len; r += nw) {
+    int lenk = 2;                                      // a power of two >= max(keep, S), <= lenb
+    while (lenk < keep || lenk < S) lenk <<= 1;
+    if (lenk > lenb) lenk = lenb;
+    for (int r = warp; r < lenk; r += nw) {
         if (r >= keep) {
             if (lane == 0) E64[r] = DBL_MAX;
             continue;
@@ -902,9 +917,9 @@ __global__ void __launch_bounds__(kBFinalThreads) bfinal_kernel(const BatchParam
         if (lane == 0) E64[r] = part;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < len; i += blockDim.x)
+    for (int i = threadIdx.x; i < lenk; i += blockDim.x)
         if (i >= keep) C[i] = kEmptyC;
-    block_sort(E64, C, len);
+    block_sort(E64, C, lenk);
     for (int k = threadIdx.x; k < S; k += blockDim.x) {
         static_cast<double*>(p.energies)[(size_t)b * S + k] = E64[k];
         p.states[(size_t)b * S + k] = C[k];
