@@ -373,7 +373,8 @@ def potts_bench(args):
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
             "higher_is_better": True, "dtype": "i32", "data": "synthetic",
             "config": {"workload": f"potts_q{q}_n{n}", "q": q, "n": n, "S": S, "configs_per_step": configs},
-            "roofline": {"bound": "alu", "kernel": "potts_walk_kernel", "achieved": achieved, "peak": peak,
+            "roofline": {"bound": "alu", "kernel": "gray_kernel" if q == 2 else "potts_walk_kernel",
+                         "achieved": achieved, "peak": peak,
                          "unit": "Gop/s", "frac": achieved / peak, "ops_per_config": 0.75, "kernel_ms": tk * 1e3},
             "clocks": clocks, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)

@@ -281,7 +281,10 @@ bf_status bf_low_spectrum_qubo(const void* a, const void* b, int n, int S, bf_dt
  * sigma_i in {0, ..., q-1}, 2 <= q <= 8, configuration integer
  * c = sum_i sigma_i q^i (base-q digits; the binary coding of Sec. 3, Eq. (4)
  * for q = 2).  q^n <= 2^62.  Ties are broken by ascending c.  For q = 2 the
- * model is an Ising instance with couplings J/2.
+ * model is an Ising instance: with J' = J, h'_i = h_i(1) - h_i(0) and
+ * C = sum_{i<j} J_ij + sum_i (h_i(0) + h_i(1)), 2 E(sigma) = E'(s) + C, and
+ * q = 2 searches above 4096 configurations run as that Ising search (BF_EUNSUPPORTED
+ * for integer h_i(1) - h_i(0) outside int32).
  *   J          device, n*n values of `dtype`, row-major; strict upper triangle read
  *   h          device, n*q values of `dtype`, row-major: h[i*q + v] = h_i(v)
  *   energies   device out, S values: int64 for BF_I32 (exact), double otherwise

@@ -472,6 +472,8 @@ namespace {
 
 struct PottsPlan {
     bool direct;
+    bool via_ising;                 // q = 2: the Ising search on the mapped instance
+    size_t inner, Jp, hp, cst, flag;
     int B, m, grid, seg_log2, list_cap, seed_per_block, seed_blocks;
     unsigned long long space, ntasks, seed_sample;
     bf::Layout L;
@@ -500,6 +502,22 @@ bf_status potts_plan(int n, int q, int S, int dtype, const bf_options* opt, Pott
     pl.direct = space <= 4096ull;
     if (pl.direct) {
         pl.bytes = sizeof(bf::WsHeader);
+        return BF_OK;
+    }
+    if (q == 2) {
+        // exact reduction to the Ising form: 2 E(sigma) = E'(s) + C with J' = J, h'_i = h_i(1) - h_i(0)
+        const bf_dtype inner_dt = dtype == BF_I32 ? BF_I32 : BF_F64;
+        Plan ip;
+        bf_status st = make_plan(n, S, inner_dt, opt, ip);
+        if (st != BF_OK) return st;
+        const size_t elt = dtype == BF_I32 ? 4 : 8;
+        pl.via_ising = true;
+        pl.inner = align256(ip.bytes);
+        pl.Jp = pl.inner;
+        pl.hp = pl.Jp + align256((size_t)n * n * elt);
+        pl.cst = pl.hp + align256((size_t)n * elt);
+        pl.flag = pl.cst + 8;
+        pl.bytes = pl.cst + 256;
         return BF_OK;
     }
     int dev = 0, sms = 0;
@@ -563,6 +581,26 @@ bf_status bf_low_spectrum_potts(const void* J, const void* h, int n, int q, int 
     if (pl.direct) {
         cudaError_t e = bf::launch_potts_direct(J, h, n, q, dtype, S, energies, out_states, hdr, stream);
         return e == cudaSuccess ? BF_OK : cuda_fail(e, "Potts direct kernel");
+    }
+    if (pl.via_ising) {
+        auto* flag = reinterpret_cast<unsigned*>(ws + pl.flag);
+        cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(unsigned), stream);
+        if (e == cudaSuccess) e = bf::launch_potts2_prep(J, h, n, (int)dtype, ws + pl.Jp, ws + pl.hp, ws + pl.cst, flag, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "two-state Potts map");
+        if (dtype == BF_I32) {
+            unsigned hflag = 0;
+            e = cudaMemcpyAsync(&hflag, flag, sizeof(hflag), cudaMemcpyDeviceToHost, stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+            if (e != cudaSuccess) return cuda_fail(e, "two-state Potts map status");
+            if (hflag) return fail(BF_EUNSUPPORTED, "h_i(1) - h_i(0) outside int32: use a float dtype");
+        }
+        const bf_dtype inner_dt = dtype == BF_I32 ? BF_I32 : BF_F64;
+        st = bf_low_spectrum(ws + pl.Jp, ws + pl.hp, n, S, inner_dt, energies, states, workspace, pl.inner, opt,
+                             stream_ptr);
+        if (st != BF_OK) return st;
+        e = bf::launch_potts2_finish(energies, S, dtype == BF_I32 ? 0 : 1, ws + pl.cst, &hdr->status, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "two-state Potts energies");
+        return BF_OK;
     }
     const bf::Layout& L = pl.L;
     auto* prep = reinterpret_cast<bf::PottsPrep*>(ws + pl.prep_off);

@@ -359,6 +359,11 @@ cudaError_t launch_set_tau(const int* E, int S, WsHeader* hdr, cudaStream_t s);
 cudaError_t launch_qubo_prep(const void* a, const void* b, int n, int dtype, void* Jout, void* hout, void* off4,
                              unsigned* flag, cudaStream_t s);
 cudaError_t launch_qubo_finish(void* F, int S, int dtype, const void* off4, unsigned* flag, cudaStream_t s);
+// Two-state Potts model as an Ising instance (k_qubo.cu): J' = J, h'_i = h_i(1) - h_i(0),
+// C = sum_{i<j} J_ij + sum_i (h_i(0) + h_i(1)); energies E = (E' + C) / 2 (same dtypes as the QUBO map)
+cudaError_t launch_potts2_prep(const void* J, const void* h, int n, int dtype, void* Jout, void* hout, void* cst,
+                               unsigned* flag, cudaStream_t s);
+cudaError_t launch_potts2_finish(void* E, int S, int dtype, const void* cst, unsigned* flag, cudaStream_t s);
 cudaError_t launch_direct(const void* J, const void* h, int n, int dtype, int S, int free_bits,
                           unsigned long long hiconst, void* energies, unsigned long long* states,
                           WsHeader* hdr, cudaStream_t s);

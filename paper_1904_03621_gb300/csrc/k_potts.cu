@@ -634,10 +634,10 @@ const void* walk_fn()
     return reinterpret_cast<const void*>(&potts_walk_kernel<Q>);
 }
 
+// q = 2 runs as an Ising search (bf_low_spectrum_potts maps it); the walk serves q = 3..8
 const void* walk_for(int q)
 {
     switch (q) {
-    case 2: return walk_fn<2>();
     case 3: return walk_fn<3>();
     case 4: return walk_fn<4>();
     case 5: return walk_fn<5>();
@@ -776,6 +776,7 @@ cudaError_t launch_potts_seed(const PottsPrep* prep, int n, int q, unsigned long
 int potts_walk_blocks_per_sm(int q, int m, int n, int list_cap)
 {
     (void)m;
+    if (q < 3 || q > kPottsMaxQ) return 0;
     const void* fn = walk_for(q);
     const size_t smem = potts_walk_smem(q, n, list_cap);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
@@ -786,12 +787,12 @@ int potts_walk_blocks_per_sm(int q, int m, int n, int list_cap)
 
 cudaError_t launch_potts_walk(const PottsParams& p, int grid, cudaStream_t s)
 {
+    if (p.q < 3 || p.q > kPottsMaxQ) return cudaErrorInvalidValue;
     const size_t smem = potts_walk_smem(p.q, p.n, p.list_cap);
     const void* fn = walk_for(p.q);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     switch (p.q) {
-    case 2: potts_walk_kernel<2><<<grid, kPottsThreads, smem, s>>>(p); break;
     case 3: potts_walk_kernel<3><<<grid, kPottsThreads, smem, s>>>(p); break;
     case 4: potts_walk_kernel<4><<<grid, kPottsThreads, smem, s>>>(p); break;
     case 5: potts_walk_kernel<5><<<grid, kPottsThreads, smem, s>>>(p); break;

@@ -61,7 +61,7 @@ def test_potts_direct_path(bf, o, q, n, S):
     assert_int_equal(e, st, e_o, st_o)
 
 
-@pytest.mark.parametrize("q,n,S", [(3, 13, 60), (4, 10, 40)])
+@pytest.mark.parametrize("q,n,S", [(3, 13, 60), (4, 10, 40), (2, 22, 60)])
 def test_potts_float(bf, o, q, n, S):
     import torch
     J, h = potts_instance(n, q, 20 + q, integer=False)
