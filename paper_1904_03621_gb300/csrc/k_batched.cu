@@ -671,16 +671,24 @@ __global__ void __launch_bounds__(kBThreads, 2) bwalk_kernel(const BatchParams p
         unsigned long long kC = kEmptyC;
         int tau_scr = 0;
         unsigned thr16 = 0;
-        auto refresh = [&]() {
-            int t = min(*(volatile int*)&p.tau[b], kE);
+        // tg: the instance threshold as read from global memory (it only decreases, so a value
+        // read earlier is still a valid bound)
+        auto refresh_with = [&](int tg) {
+            int t = min(tg, kE);
             long long ts = (long long)t + W;
             tau_scr = (int)(ts > (1ll << 30) ? (1ll << 30) : ts);
             thr16 = threshold16(tau_scr);
         };
+        auto refresh = [&]() { refresh_with(*(volatile int*)&p.tau[b]); };
         refresh();
         unsigned long long cmid = 0ull;
         const unsigned nblocks = 1u << m;
         for (unsigned ub = 0; ub < nblocks; ++ub) {
+            // every fourth block re-reads the instance threshold: the load is issued here and
+            // consumed after the unrolled walk, so its latency is hidden
+            const bool reread = (ub & 3u) == 3u;
+            int tg_early = 0;
+            if (reread) tg_early = *(volatile int*)&p.tau[b];
             pk.Xa = pack_energy(E0[0], E0[1]);
             pk.Xb = pack_energy(E0[2], E0[3]);
             pk.M = __vminu2(pk.Xa, pk.Xb);
@@ -737,7 +745,7 @@ __global__ void __launch_bounds__(kBThreads, 2) bwalk_kernel(const BatchParams p
                     refresh();
                 }
             }
-            if ((ub & 3u) == 3u) refresh();
+            if (reread) refresh_with(tg_early);
             if ((ub % kBSyncEvery) == kBSyncEvery - 1) __syncthreads();   // keep the warps on the same code
             // flip one middle spin
             if (ub + 1 < nblocks) {
