@@ -14,7 +14,11 @@ e2e        the same metric through the public API with host buffers: pinned
 roofline   the enumeration kernel (gray_kernel), timed live with CUDA events
            recorded by the library around that kernel: ALU lane-instructions
            required by the inner loop (0.75 per configuration) / kernel time,
-           against the integer-ALU issue peak of the GPU
+           against the peak of that instruction mix from the issue rates the
+           library's probe measures on this GPU in the same run
+configs    the other single-instance configurations (n=20 float, n=32 integer,
+           the n=48 instance on 64 stored subspaces), timed and compared with
+           stored oracle results: max |E_gpu - E_oracle| per configuration
 cpu_baseline  the CPU oracle timed on this host's cores on a bounded sample
            (one fixed-prefix subspace of the same instance)
 
@@ -39,9 +43,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "configs/s with exact top-S at N=48, % of roofline; batched instances/s"
 UNIT = "configs/s"
-SMS = 152
-ALU_LANES_PER_SM = 64          # integer ALU pipe: 16 lanes per SM sub-partition (probe-measured)
 ALU_OPS_PER_CONFIG = 0.75      # inner loop: one IADD3 per 2 configurations + one 3-input 16x2 min per 4
+IADD3_PER_CONFIG, VMNMX_PER_CONFIG = 0.5, 0.25
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+SCREEN = ("exact int32 fixed point (scale 2^q, rounding residual bound, candidate window) with a two-lane "
+          "16-bit pre-filter; every candidate re-evaluated in FP64 (Eq. (1)) before the final selection")
 CPU_SAMPLE_FREE_BITS = 25      # oracle baseline: one subspace of 2^25 configurations
 REF_STEP_FREE_BITS = 22        # reference arm: one subspace of 2^22 configurations per step
 
@@ -82,6 +88,54 @@ def workload(name: str, rank: int):
         J, h = instances.dense_gaussian(n, rank, h_std=0.1)
         return J, h, 1000, f"n={n} fully connected, J~N(0,1), h~N(0,0.1^2), S=1000 (development size)"
     raise SystemExit(f"unknown workload {name}")
+
+
+def read_golden(name):
+    """{block: (energies, states)} of a stored oracle result (tests/golden, gzip text)."""
+    import gzip
+    out = {}
+    with gzip.open(os.path.join(GOLDEN, name), "rt") as f:
+        for line in f:
+            if line.startswith("#"):
+                continue
+            b, _, e, c = line.split()
+            rec = out.setdefault(int(b), ([], []))
+            rec[0].append(float(e) if any(x in e for x in ".ein") else int(e))
+            rec[1].append(int(c))
+    return {b: (np.array(v[0]), np.array(v[1], dtype=np.uint64)) for b, v in out.items()}
+
+
+def max_err(en_gpu, st_gpu, en_or, st_or):
+    """max |E_gpu - E_oracle| rank by rank, and how many ranks hold another state than the oracle's."""
+    en_gpu = np.asarray(en_gpu, dtype=np.float64)
+    en_or = np.asarray(en_or, dtype=np.float64)[:len(en_gpu)]
+    st_or = np.asarray(st_or, dtype=np.uint64)[:len(en_gpu)]
+    return float(np.abs(en_gpu - en_or).max()), int((np.asarray(st_gpu, dtype=np.uint64) != st_or).sum())
+
+
+def tolerance(J, h):
+    return 1e-9 * float(np.abs(np.triu(np.asarray(J, dtype=np.float64), 1)).sum()
+                        + np.abs(np.asarray(h, dtype=np.float64)).sum())
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def walk_peak(rates, sm_max_mhz):
+    """Peak rate of the walk's instruction mix (per configuration: 0.5 IADD3 + 0.25 16x2 minimum) from
+    the measured issue rates: configurations/s x 0.75 = lane-instructions/s at the maximum SM clock."""
+    lanes = ALU_OPS_PER_CONFIG / (IADD3_PER_CONFIG / rates["iadd3_lanes_per_clk"]
+                                  + VMNMX_PER_CONFIG / rates["vmnmx_lanes_per_clk"])
+    return rates["sms"] * lanes * sm_max_mhz * 1e6, lanes
 
 
 def peaks():
@@ -154,6 +208,7 @@ def cpu_baseline(J, h, S):
     o.low_spectrum(J, h, S, fixed_bits=fb, fixed_value=(1 << fb) // 3)
     dt = time.perf_counter() - t
     return {"value": (1 << CPU_SAMPLE_FREE_BITS) / dt, "unit": UNIT, "cores": o.num_threads, "kind": "oracle",
+            "cpu_model": cpu_model(),
             "sample": f"one subspace of 2^{CPU_SAMPLE_FREE_BITS} configurations (top {fb} bits fixed) of the "
                       f"same instance, S={S}, {dt:.1f} s"}
 
@@ -181,7 +236,7 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": args.workload, "description": desc, "sample": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": o.num_threads, "kind": "oracle",
-                             "sample": sample},
+                             "cpu_model": cpu_model(), "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -217,6 +272,13 @@ def batched_section(api, torch, dev, steps, warmup):
     from paper_1904_03621_gb300 import _lib
     lib = _lib.load()
     _lib.check(lib.bf_workspace_status(ws.data_ptr(), None), lib)
+    # error against the stored FP64 oracle results of 96 sampled instances
+    gold = read_golden("batched_sample_S10.txt.gz")
+    en_np, st_np = en.cpu().numpy(), st.cpu().numpy().view(np.uint64)
+    errs = [max_err(en_np[i], st_np[i], *gold[i]) for i in sorted(gold)]
+    acc4 = {"max_abs_err_vs_oracle": max(e for e, _ in errs), "rank_state_mismatches": sum(m for _, m in errs),
+            "max_tolerance": max(tolerance(insts[i][0], insts[i][1]) for i in gold),
+            "sample": f"{len(gold)} stored oracle results (indices drawn with default_rng(2)), S=10"}
     # plain path: one bf_low_spectrum call per instance (first 64 instances of each kind)
     sample = list(range(64)) + list(range(B // 2, B // 2 + 64))
     t0 = time.perf_counter()
@@ -232,11 +294,33 @@ def batched_section(api, torch, dev, steps, warmup):
            "autotuned": tuned,
            "steps": steps, "plain_instances_per_s": plain_ips,
            "plain_sample": f"{len(sample)} instances, one bf_low_spectrum call each",
-           "speedup_vs_plain": (B / (ms * 1e-3)) / plain_ips}
-    # backward: 256 x n=28 (FP32), S=32
+           "speedup_vs_plain": (B / (ms * 1e-3)) / plain_ips, "accuracy": acc4}
+    # differentiable form: 256 x n=28 (FP32 inputs), S=32; forward (batched search) then backward
     ginst, w = instances.grad_256()
     Jg, Jgo, hg, hgo, ng, ngm = api.pack_batch(ginst, dtype=torch.float32, device=dev)
-    eng, stg = api.low_spectrum_batched(Jg, Jgo, hg, hgo, ng, 32, n_max=ngm)
+    wsg = torch.empty(api.batched_workspace_size(len(ginst), ngm, 32, torch.float32), dtype=torch.uint8, device=dev)
+    eng = torch.empty(len(ginst), 32, dtype=torch.float64, device=dev)
+    stg = torch.empty(len(ginst), 32, dtype=torch.int64, device=dev)
+    for _ in range(2):
+        api.low_spectrum_batched(Jg, Jgo, hg, hgo, ng, 32, n_max=ngm, workspace=wsg, out=(eng, stg))
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        api.low_spectrum_batched(Jg, Jgo, hg, hgo, ng, 32, n_max=ngm, workspace=wsg, out=(eng, stg), check=False)
+    e1.record()
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / steps
+    _lib.check(lib.bf_workspace_status(wsg.data_ptr(), None), lib)
+    gold5 = read_golden("grad_sample_S32.txt.gz")
+    e5, s5 = eng.cpu().numpy(), stg.cpu().numpy().view(np.uint64)
+    errs5 = [max_err(e5[i], s5[i], *gold5[i]) for i in sorted(gold5)]
+    out["forward_256_n28"] = {
+        "workload": "grad_256: 256 x n=28 fully connected, J,h~N(0,1) as FP32, S=32, one batched call",
+        "ms": fwd_ms, "configs_per_s": 256 * 2.0 ** 28 / (fwd_ms * 1e-3), "instances_per_s": 256 / (fwd_ms * 1e-3),
+        "accuracy": {"max_abs_err_vs_oracle": max(e for e, _ in errs5),
+                     "rank_state_mismatches": sum(m for _, m in errs5),
+                     "max_tolerance": max(tolerance(ginst[i][0], ginst[i][1]) for i in gold5),
+                     "sample": f"{len(gold5)} stored FP64 oracle results (indices drawn with default_rng(2))"}}
     wt = torch.from_numpy(w).to(dev)
     for _ in range(2):
         api.low_spectrum_backward(stg, wt, ng, Jgo, hgo, Jg.numel(), hg.numel(), dtype=torch.float32)
@@ -262,6 +346,64 @@ def batched_section(api, torch, dev, steps, warmup):
     out["backward"] = {"workload": "grad_256: 256 x n=28, S=32, L=sum w_k E_k", "backward_ms": back_ms,
                        "plain_torch_backward_ms": plain_back_ms, "speedup_vs_plain": plain_back_ms / back_ms}
     return out
+
+
+def config_checks(api, torch, dev, reps=10):
+    """The other single-instance configurations, each timed (CUDA events, inputs in HBM, median of
+    `reps` calls) and compared with stored FP64 / int64 oracle results: the error against the oracle
+    per configuration."""
+    from paper_1904_03621_gb300 import instances
+    stream = torch.cuda.current_stream()
+
+    def timed(J, h, S, **kw):
+        Jd = torch.from_numpy(np.ascontiguousarray(J)).to(dev)
+        hd = torch.from_numpy(np.ascontiguousarray(h)).to(dev)
+        ws = torch.empty(api.workspace_size(J.shape[0], S, Jd.dtype, **kw), dtype=torch.uint8, device=dev)
+        times = []
+        for it in range(reps + 2):
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            en, st = api.low_spectrum(Jd, hd, S, workspace=ws, check=False, **kw)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            if it >= 2:
+                times.append(ev0.elapsed_time(ev1))
+        from paper_1904_03621_gb300 import _lib
+        _lib.check(_lib.load().bf_workspace_status(ws.data_ptr(), None))
+        return float(np.median(times)), en.cpu().numpy(), api.states_u64(st)
+
+    out = {}
+    J, h = instances.plain_n20()
+    ms, en, st = timed(J, h, 10)
+    g = read_golden("plain_n20_S10.txt.gz")[0]
+    err, mis = max_err(en, st, *g)
+    out["plain_n20"] = {"workload": "n=20 fully connected, J,h~N(0,1) FP64, S=10", "ms": ms,
+                        "configs_per_s": 2.0 ** 20 / (ms * 1e-3), "max_abs_err_vs_oracle": err,
+                        "rank_state_mismatches": mis, "tolerance": tolerance(J, h)}
+    J, h = instances.int_n32()
+    ms, en, st = timed(J, h, 100)
+    g = read_golden("int_n32_S100.txt.gz")[0]
+    out["int_n32"] = {"workload": "n=32 fully connected, J uniform in {-1,+1} int32, h=0, S=100", "ms": ms,
+                      "configs_per_s": 2.0 ** 32 / (ms * 1e-3),
+                      "bit_exact": bool(np.array_equal(en, g[0]) and np.array_equal(st, g[1]))}
+    J, h = instances.float_n48()
+    gold = read_golden("float_n48_sub24_S1000.txt.gz")
+    first = sorted(gold)[0]
+    ms, _, _ = timed(J, h, 1000, fixed_bits=24, fixed_value=first, inner_bits=10)
+    errs = [max_err(*_single(api, torch, dev, J, h, 1000, fixed_bits=24, fixed_value=v, inner_bits=10), *gold[v])
+            for v in sorted(gold)]
+    out["float_n48_subspaces"] = {
+        "workload": "n=48 float instance on 64 stored fixed-prefix subspaces (top 24 bits fixed), S=1000, "
+                    "10 inner spins (the kernel of the full search)",
+        "max_abs_err_vs_oracle": max(e for e, _ in errs), "rank_state_mismatches": sum(m for _, m in errs),
+        "tolerance": tolerance(J, h), "ms_per_subspace": ms}
+    return out
+
+
+def _single(api, torch, dev, J, h, S, **kw):
+    en, st = api.low_spectrum(torch.from_numpy(J).to(dev), torch.from_numpy(h).to(dev), S, **kw)
+    return en.cpu().numpy(), api.states_u64(st)
 
 
 FIG3_K = {16: 100, 18: 100, 20: 100, 22: 100, 24: 100, 26: 100, 28: 100, 30: 100, 32: 100, 34: 100, 36: 100,
@@ -365,9 +507,8 @@ def potts_bench(args):
     cpu = {"value": float(q) ** n_cpu / dt_cpu, "unit": "configs/s", "cores": o.num_threads, "kind": "oracle",
            "sample": f"all {q}^{n_cpu} configurations of the leading {n_cpu}-spin block of the instance, S={S}, "
                      f"{dt_cpu:.1f} s"}
-    pk = peaks()
-    mhz = clocks.get("sm_max_mhz") or 2070.0
-    peak = 152 * 64 * mhz * 1e6 / 1e9
+    mhz = clocks.get("sm_max_mhz") or float(peaks()[0].get("sm_max_mhz", 2070.0))
+    peak = walk_peak(api.issue_rates(), mhz)[0] / 1e9
     achieved = 0.75 * configs / tk / 1e9
     line = {"metric": "Potts configurations/s (exact top-S)", "value": configs / t, "unit": "configs/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
@@ -494,6 +635,23 @@ def checkpoint_bench(args):
     return 0 if same else 1
 
 
+def issue_rates_line(args):
+    """The issue-rate probe alone (bf_measure_issue_rates): one JSON line with lane-instructions per
+    clock per SM of each instruction class and the walk's peak at the measured maximum SM clock."""
+    import torch  # noqa: F401
+    from paper_1904_03621_gb300 import build
+    build.build()
+    from paper_1904_03621_gb300 import api
+    runs = [api.issue_rates() for _ in range(max(args.steps, 1))]
+    med = {k: float(np.median([r[k] for r in runs])) for k in runs[0]}
+    med["sms"] = int(med["sms"])
+    sm_max = float(peaks()[0].get("sm_max_mhz", 2070.0))
+    peak, lanes = walk_peak(med, sm_max)
+    print(json.dumps({"metric": "issue rates (lane-instructions per clock per SM)", "rates": med, "runs": runs,
+                      "walk_lanes_per_clk": lanes, "walk_peak_gops": peak / 1e9, "sm_max_mhz": sm_max}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -515,7 +673,11 @@ def main():
                     help="cost of the checkpointed (chunked) search against one call, n = 44")
     ap.add_argument("--batched-only", action="store_true",
                     help="time only the 4096-instance batched search (one JSON line)")
+    ap.add_argument("--issue-rates", action="store_true",
+                    help="measure the integer / FP32 issue rates (the roofline denominator) and print them")
     args = ap.parse_args()
+    if args.issue_rates:
+        return issue_rates_line(args)
     if args.fig3:
         return fig3_sweep(args)
     if args.batched_only:
@@ -576,6 +738,7 @@ def main():
         return ev0, ev1
 
     lib = _lib.load()
+    rates = api.issue_rates()           # roofline denominator: issue rates measured on this GPU
     for _ in range(args.warmup):
         step(0)
         torch.cuda.synchronize()
@@ -616,7 +779,7 @@ def main():
     e2e_value = total_configs / e2e_s
     pk, pk_kind = peaks()
     sm_max_mhz = float(pk.get("sm_max_mhz", 2070.0))
-    peak_ops = SMS * ALU_LANES_PER_SM * sm_max_mhz * 1e6
+    peak_ops, walk_lanes = walk_peak(rates, sm_max_mhz)
     gray_s = gray_ms * 1e-3 / args.steps
     if args.variant == "tc":
         # one 128 x 256 x 16 BF16 MMA per 32768 configurations: 2 * 16 flops per configuration,
@@ -629,19 +792,23 @@ def main():
                           "kernel_ms": gray_ms / args.steps, "kernel_share_of_step": gray_ms / dev_ms}
     else:
         achieved = ALU_OPS_PER_CONFIG * configs_per_step / gray_s
-        roofline_block = {"bound": "alu", "kernel": "gray_kernel", "achieved": achieved / 1e9,
+        roofline_block = {"bound": "alu", "kernel": "gray_kernel<10>", "achieved": achieved / 1e9,
                           "peak": peak_ops / 1e9, "unit": "Gop/s", "frac": achieved / peak_ops,
                           "traffic": gray_traffic(args.workload),
                           "ops_per_config": ALU_OPS_PER_CONFIG,
-                          "peak_basis": f"{SMS} SMs x {ALU_LANES_PER_SM} integer-ALU lanes x {sm_max_mhz:.0f} MHz "
+                          "peak_basis": f"{rates['sms']} SMs x {walk_lanes:.2f} lane-instructions/clock/SM of the "
+                                        f"walk's mix (0.5 IADD3 + 0.25 16x2 min per configuration, issue rates "
+                                        f"measured by bf_measure_issue_rates in this run) x {sm_max_mhz:.0f} MHz "
                                         f"(sm_max_mhz {pk_kind})",
+                          "issue_rates": rates,
                           "kernel_ms": gray_ms / args.steps,
                           "kernel_share_of_step": gray_ms / dev_ms}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "i32", "data": "synthetic",
-        "config": {"workload": args.workload, "description": desc, "n": n, "S": S,
+        "scaling": "weak", "vs_baseline": None, "dtype": "i32" if Jh.dtype == torch.int32 else "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc, "n": n, "S": S, "screen": SCREEN,
                    "configs_per_step": configs_per_step, "l2": "flushed between steps (256 MB write)",
                    "instances": "one per rank, seed = rank"},
         "roofline": roofline_block,
@@ -653,6 +820,7 @@ def main():
     }
     if not args.no_batched:
         line["batched"] = batched_section(api, torch, dev, max(args.steps, 3), max(args.warmup, 3))
+        line["configs"] = config_checks(api, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(J, h, S)
     if rank == 0:

@@ -94,6 +94,11 @@ typedef enum {
  *                the kernel then stops, frees its tensor memory and the call's
  *                workspace status is BF_ETIMEOUT.  The CUDA context stays
  *                usable.  Ignored by the other kernels.
+ *   inner_bits   spins walked by the fully unrolled block of the Gray-code walk:
+ *                0 = automatic (the autotuned choice for this device and search
+ *                size, else 10 for searches of at least 2^42 configurations and
+ *                9 below), or 9 or 10 (10 needs n >= 14).  Results do not depend
+ *                on it.  Ignored by the tensor-core variant.
  */
 typedef struct {
     int32_t variant;
@@ -104,7 +109,8 @@ typedef struct {
     int32_t spill_log2;
     int32_t profile;
     int32_t stall_test;
-    int32_t reserved[5];
+    int32_t inner_bits;
+    int32_t reserved[4];
 } bf_options;
 
 /* Largest S accepted by bf_low_spectrum. */
@@ -127,10 +133,18 @@ size_t bf_workspace_size(int n, int S, bf_dtype dtype, const bf_options* opt);
  *   states     device out, S configuration integers
  *   workspace  device, >= bf_workspace_size(...) bytes, 256-byte aligned
  *   stream     cudaStream_t (NULL = legacy default stream)
- * Queues the whole search on `stream`.  The call blocks once, after a small
- * preparation kernel, to copy its per-instance constants into the launch
- * parameters of the enumeration kernel; it is therefore not capturable in a
- * CUDA graph.  Returns BF_OK when the work was queued.
+ * Queues the whole search on `stream` and returns without synchronising
+ * (BF_OK when the work was queued); the call can be captured in a CUDA graph
+ * and replayed with new values in J and h (same n, S, dtype and options).
+ * Instances outside the int32 fixed-point range are reported by
+ * bf_workspace_status (BF_EUNSUPPORTED).
+ * Streams: the enumeration kernel reads its per-instance step increments from
+ * one table per device, which the call fills from the workspace just before
+ * the kernel.  Searches queued on different streams are ordered around that
+ * table by the library (the next fill waits for the previous enumeration
+ * kernel on the device).  Work queued while a stream is being captured is not
+ * ordered that way: a graph holding this call must not run at the same time
+ * as another search on the same device.
  */
 bf_status bf_low_spectrum(const void* J, const void* h, int n, int S, bf_dtype dtype,
                           void* energies, uint64_t* states,
@@ -151,14 +165,17 @@ bf_status bf_low_spectrum(const void* J, const void* h, int n, int S, bf_dtype d
  * the process exits.  It calls no cudaMalloc / cudaFree.
  *   - The first call on a device (with that device current) looks up the
  *     array's device address once; make that first call before any stream
- *     capture.
+ *     capture.  The address is kept for the life of the process: after a
+ *     cudaDeviceReset() of that device, which destroys the array with the
+ *     context, this entry point must not be called again in the process.
  *   - Searches needing more than 4 MiB (at the default grid roughly S > 256,
  *     or a spill area larger than opt->spill_log2, default 16 here) return
  *     BF_EUNSUPPORTED without launching anything.
  *   - Every call shares the array: calls whose work overlaps on the GPU race
  *     and give undefined results.  Each call clears what it needs.
- *   - Unlike bf_low_spectrum, the call waits for its work to finish and
- *     returns the device-side status (BF_EOVERFLOW etc.) directly.
+ *   - Unlike bf_low_spectrum, every call synchronises `stream`: it waits
+ *     for its work to finish and returns the device-side status
+ *     (BF_EOVERFLOW etc.) directly.
  */
 bf_status bf_low_spectrum_noalloc(const void* J, const void* h, int n, int S, bf_dtype dtype,
                                   void* energies, uint64_t* states,
@@ -265,8 +282,8 @@ size_t bf_qubo_workspace_size(int n, int S, bf_dtype dtype, const bf_options* op
  *   workspace  device, >= bf_qubo_workspace_size(...) bytes, 256-byte aligned
  * Other arguments and options as for bf_low_spectrum (float inputs are
  * converted to a double Ising instance first).  BF_I32 inputs whose
- * 2 b_i + sum_j a_ij leaves int32 return BF_EUNSUPPORTED.  The call
- * synchronises the stream once more than bf_low_spectrum (integer inputs).
+ * 2 b_i + sum_j a_ij leaves int32 are reported by bf_workspace_status
+ * (BF_EUNSUPPORTED).  Like bf_low_spectrum the call does not synchronise.
  */
 bf_status bf_low_spectrum_qubo(const void* a, const void* b, int n, int S, bf_dtype dtype, void* F, uint64_t* states,
                                void* workspace, size_t workspace_bytes, const bf_options* opt, void* stream);
@@ -366,6 +383,33 @@ bf_status bf_last_profile(float* enumeration_ms);
 
 /* Number of kernels this library has launched in the process so far. */
 int64_t bf_launch_count(void);
+
+/*
+ * Measured issue rates of this GPU (measurement hook, no counterpart in the
+ * paper): the denominators of the enumeration kernels' roofline, whose work
+ * is counted in integer-ALU lane-instructions per configuration.  Each rate is
+ * lane-instructions per clock per SM of one instruction class, from one
+ * 1024-thread block per SM running 8 independent dependency chains per
+ * thread (x_t = op(x_{t-1}, x_{t-2}, x_{t-4})), cycles read on the SM.
+ */
+typedef struct {
+    int32_t sms;                  /* multiprocessors (device query) */
+    double sm_clock_mhz;          /* SM cycles / CUDA-event time of the probe launches */
+    double iadd3_lanes_per_clk;   /* 3-input 32-bit integer add */
+    double lop3_lanes_per_clk;    /* 3-input logic operation (integer ALU only) */
+    double vmnmx_lanes_per_clk;   /* 16x2 minimum / maximum */
+    double ffma_lanes_per_clk;    /* FP32 fused multiply-add (for comparison) */
+} bf_issue_rates;
+
+/* Device workspace bytes bf_measure_issue_rates needs. */
+size_t bf_issue_rates_workspace_size(void);
+
+/*
+ * Runs the probe kernels on `stream` (two launches per class, about 10 ms in
+ * all) and fills *out.  workspace: device, >= bf_issue_rates_workspace_size()
+ * bytes.  Synchronises the stream.
+ */
+bf_status bf_measure_issue_rates(void* workspace, size_t workspace_bytes, bf_issue_rates* out, void* stream);
 
 /*
  * bf_merge_lists -- the S lowest records of k result lists (host memory).

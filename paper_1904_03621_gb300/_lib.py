@@ -19,14 +19,22 @@ EXPORTS = ["bf_workspace_size", "bf_low_spectrum", "bf_low_spectrum_noalloc", "b
            "bf_low_spectrum_batched", "bf_autotune_batched", "bf_low_spectrum_backward", "bf_qubo_workspace_size",
            "bf_low_spectrum_qubo", "bf_potts_workspace_size", "bf_low_spectrum_potts", "bf_instance_digest", "bf_cursor_bytes", "bf_cursor_init",
            "bf_cursor_workspace_size", "bf_cursor_step", "bf_cursor_state", "bf_workspace_status",
-           "bf_last_profile", "bf_launch_count", "bf_merge_lists", "bf_status_string", "bf_last_error_detail",
+           "bf_last_profile", "bf_launch_count", "bf_issue_rates_workspace_size", "bf_measure_issue_rates",
+           "bf_merge_lists", "bf_status_string", "bf_last_error_detail",
            "bf_version"]
 
 
 class Options(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("fixed_bits", ctypes.c_int32), ("fixed_value", ctypes.c_uint64),
                 ("task_log2", ctypes.c_int32), ("grid_blocks", ctypes.c_int32), ("spill_log2", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("stall_test", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("profile", ctypes.c_int32), ("stall_test", ctypes.c_int32), ("inner_bits", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
+class IssueRates(ctypes.Structure):
+    _fields_ = [("sms", ctypes.c_int32), ("sm_clock_mhz", ctypes.c_double), ("iadd3_lanes_per_clk", ctypes.c_double),
+                ("lop3_lanes_per_clk", ctypes.c_double), ("vmnmx_lanes_per_clk", ctypes.c_double),
+                ("ffma_lanes_per_clk", ctypes.c_double)]
 
 
 class BFError(RuntimeError):
@@ -100,6 +108,10 @@ def load(path: str | None = None):
     lib.bf_last_profile.argtypes = [ctypes.POINTER(ctypes.c_float)]
     lib.bf_launch_count.restype = ctypes.c_int64
     lib.bf_launch_count.argtypes = []
+    lib.bf_issue_rates_workspace_size.restype = sz
+    lib.bf_issue_rates_workspace_size.argtypes = []
+    lib.bf_measure_issue_rates.restype = i32
+    lib.bf_measure_issue_rates.argtypes = [vp, sz, ctypes.POINTER(IssueRates), vp]
     if path is None:
         _lib = lib
     return lib

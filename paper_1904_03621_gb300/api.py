@@ -21,10 +21,10 @@ def _stream_handle(stream):
 
 
 def _options(variant=0, fixed_bits=0, fixed_value=0, task_log2=0, grid_blocks=0, spill_log2=0, profile=0,
-             stall_test=0):
+             stall_test=0, inner_bits=0):
     return _lib.Options(variant=variant, fixed_bits=fixed_bits, fixed_value=fixed_value,
                         task_log2=task_log2, grid_blocks=grid_blocks, spill_log2=spill_log2, profile=profile,
-                        stall_test=stall_test)
+                        stall_test=stall_test, inner_bits=inner_bits)
 
 
 def workspace_size(n: int, S: int, dtype: torch.dtype, **opts) -> int:
@@ -39,7 +39,7 @@ def workspace_size(n: int, S: int, dtype: torch.dtype, **opts) -> int:
 def low_spectrum(J: torch.Tensor, h: torch.Tensor, S: int, *, variant: int = 0, fixed_bits: int = 0,
                  fixed_value: int = 0, task_log2: int = 0, grid_blocks: int = 0, spill_log2: int = 0,
                  profile: int = 0, stream=None, workspace: torch.Tensor | None = None, check: bool = True,
-                 out: tuple | None = None, stall_test: int = 0):
+                 out: tuple | None = None, stall_test: int = 0, inner_bits: int = 0):
     """S lowest (energy, configuration) pairs of E(s) = sum_{i<j} J_ij s_i s_j + sum_i h_i s_i.
 
     J: (n, n) CUDA tensor (int32, float32 or float64), strict upper triangle read.
@@ -56,7 +56,8 @@ def low_spectrum(J: torch.Tensor, h: torch.Tensor, S: int, *, variant: int = 0, 
     n = J.shape[0]
     J = J.contiguous()
     h = h.contiguous()
-    o = _options(variant, fixed_bits, fixed_value, task_log2, grid_blocks, spill_log2, profile, stall_test)
+    o = _options(variant, fixed_bits, fixed_value, task_log2, grid_blocks, spill_log2, profile, stall_test,
+                 inner_bits)
     nbytes = lib.bf_workspace_size(n, S, _DTYPES[J.dtype], ctypes.byref(o))
     if nbytes == 0:
         # the call validates its arguments before touching any pointer: get the exact status
@@ -168,6 +169,17 @@ def last_profile_ms() -> float:
     ms = ctypes.c_float(0.0)
     _lib.check(lib.bf_last_profile(ctypes.byref(ms)), lib)
     return float(ms.value)
+
+
+def issue_rates(stream=None) -> dict:
+    """Measured issue rates of the current GPU (bf_measure_issue_rates): lane-instructions per
+    clock per SM of 3-input integer adds, 3-input logic operations, 16x2 min/max and FP32 FMA,
+    the SM count and the SM clock seen by the probe."""
+    lib = _lib.load()
+    ws = torch.empty(int(lib.bf_issue_rates_workspace_size()), dtype=torch.uint8, device="cuda")
+    r = _lib.IssueRates()
+    _lib.check(lib.bf_measure_issue_rates(ws.data_ptr(), ws.numel(), ctypes.byref(r), _stream_handle(stream)), lib)
+    return {k: getattr(r, k) for k, _ in _lib.IssueRates._fields_}
 
 
 def launch_count() -> int:

@@ -119,6 +119,10 @@ bf_status make_plan(int n, int S, int dtype, const bf_options* opt, Plan& pl)
     if (S > BF_MAX_S) return fail(BF_EUNSUPPORTED, "S=%d exceeds BF_MAX_S=%d", S, BF_MAX_S);
     if (o.task_log2 < 0 || o.grid_blocks < 0) return fail(BF_EINVAL, "negative task_log2 or grid_blocks");
     if (o.spill_log2 < 0 || o.spill_log2 > 28) return fail(BF_EINVAL, "spill_log2=%d outside [0, 28]", o.spill_log2);
+    if (o.inner_bits != 0 && o.inner_bits != 9 && o.inner_bits != 10)
+        return fail(BF_EINVAL, "inner_bits=%d is not 0, 9 or 10", o.inner_bits);
+    // the walk keeps the local fields of the kKeep spins above the inner block
+    if (o.inner_bits == 10 && n < 10 + bf::kKeep) return fail(BF_EINVAL, "inner_bits=10 needs n >= 14");
 
     pl = Plan{};
     pl.n = n;
@@ -160,7 +164,7 @@ bf_status make_plan(int n, int S, int dtype, const bf_options* opt, Plan& pl)
         int bps = bf::gray_blocks_per_sm(pl.list_cap);
         if (bps < 1) return fail(BF_ECUDA, "enumeration kernel does not fit on an SM (S=%d)", S);
         pl.grid = o.grid_blocks ? o.grid_blocks : sms * bps;
-        pl.inner_bits = bf::gray_inner_bits(free_bits);
+        pl.inner_bits = o.inner_bits ? o.inner_bits : bf::gray_inner_bits(free_bits);
         const int walk_bits = free_bits - pl.inner_bits;           // middle + task-index bits
         if (o.task_log2) {
             pl.m = std::min(std::max(o.task_log2 - pl.inner_bits, 0), walk_bits);
@@ -197,12 +201,12 @@ bf_status make_plan(int n, int S, int dtype, const bf_options* opt, Plan& pl)
 
 // Pairwise merge rounds until one list is left; returns true if it is in A.
 cudaError_t merge_tree(int* AE, unsigned long long* AC, int* BE, unsigned long long* BC, int nin, int cap, int S,
-                       int W, bf::WsHeader* hdr, cudaStream_t stream, bool& in_a)
+                       int W, bf::WsHeader* hdr, cudaStream_t stream, bool& in_a, const int* Wp = nullptr)
 {
     in_a = true;
     while (nin > 1) {
-        cudaError_t e = in_a ? bf::launch_merge_round(AE, AC, nin, BE, BC, cap, S, W, hdr, stream)
-                             : bf::launch_merge_round(BE, BC, nin, AE, AC, cap, S, W, hdr, stream);
+        cudaError_t e = in_a ? bf::launch_merge_round(AE, AC, nin, BE, BC, cap, S, W, hdr, stream, Wp)
+                             : bf::launch_merge_round(BE, BC, nin, AE, AC, cap, S, W, hdr, stream, Wp);
         if (e != cudaSuccess) return e;
         nin = (nin + 1) / 2;
         in_a = !in_a;
@@ -243,6 +247,12 @@ namespace bf {
 bf_status report(bf_status s, const char* detail) { return fail(s, "%s", detail); }
 }  // namespace bf
 
+namespace {
+bf_status low_spectrum_impl(const void* J, const void* h, int n, int S, bf_dtype dtype, void* energies,
+                            uint64_t* states, void* workspace, size_t workspace_bytes, const bf_options* opt,
+                            void* stream_ptr, const unsigned* range_flag);
+}  // namespace
+
 extern "C" {
 
 size_t bf_workspace_size(int n, int S, bf_dtype dtype, const bf_options* opt)
@@ -255,6 +265,20 @@ size_t bf_workspace_size(int n, int S, bf_dtype dtype, const bf_options* opt)
 bf_status bf_low_spectrum(const void* J, const void* h, int n, int S, bf_dtype dtype, void* energies,
                           uint64_t* states, void* workspace, size_t workspace_bytes, const bf_options* opt,
                           void* stream_ptr)
+{
+    return low_spectrum_impl(J, h, n, S, dtype, energies, states, workspace, workspace_bytes, opt, stream_ptr,
+                             nullptr);
+}
+
+}  // extern "C"
+
+namespace {
+
+// range_flag (device, optional): a nonzero value found there when preparation runs marks the
+// instance as out of range (the QUBO map's int32 check), without a host round trip
+bf_status low_spectrum_impl(const void* J, const void* h, int n, int S, bf_dtype dtype, void* energies,
+                            uint64_t* states, void* workspace, size_t workspace_bytes, const bf_options* opt,
+                            void* stream_ptr, const unsigned* range_flag)
 {
     g_detail.clear();
     Plan pl;
@@ -287,14 +311,11 @@ bf_status bf_low_spectrum(const void* J, const void* h, int n, int S, bf_dtype d
     // the tensor-core variant needs 4x headroom: its cross coefficients reach 4 sum|J|
     pp.emq_log2 = pl.variant == BF_VARIANT_TC ? bf::kEmqLog2 - 2 : bf::kEmqLog2;
     pp.inner_bits = pl.variant == BF_VARIANT_TC ? 9 : pl.inner_bits;
+    pp.range_flag = range_flag;
     pp.prep = prep;
     pp.hdr = hdr;
     cudaError_t e = bf::launch_prep(pp, stream);
     if (e != cudaSuccess) return cuda_fail(e, "prep kernel");
-
-    SideStream* side = nullptr;
-    e = side_mark(stream, side);
-    if (e != cudaSuccess) return cuda_fail(e, "prep event");
 
     int* AE = reinterpret_cast<int*>(ws + L.listA_E);
     auto* AC = reinterpret_cast<unsigned long long*>(ws + L.listA_C);
@@ -321,16 +342,15 @@ bf_status bf_low_spectrum(const void* J, const void* h, int n, int S, bf_dtype d
         if (e != cudaSuccess) return cuda_fail(e, "local-search seed");
     }
 
-    // The per-instance increments of the unrolled walk become kernel
-    // parameters (constant bank operands of the inner loop); the seed runs meanwhile.
-    bf::PrepLaunch hl;
-    e = side_copy(&hl, &prep->L, sizeof(hl), side);
-    if (e != cudaSuccess) return cuda_fail(e, "prep copy");
-    if (hl.status & bf::kErrRange)
-        return fail(BF_EUNSUPPORTED, "couplings outside the int32 fixed-point range (sum|J|+sum|h| = %g)", hl.emax);
+    // Everything the walk needs from preparation stays on the device: the increments of the
+    // unrolled steps go to a constant table (launch_gray), the window W and the scale q are read
+    // from the workspace by the kernels, and an instance outside the fixed-point range sets a
+    // status bit that stops the walk and is reported by bf_workspace_status.  No host
+    // synchronisation: the call can be captured in a CUDA graph.
+    const int* Wd = &prep->L.W;
+    const int* qd = &prep->L.q;
 
     bf::GrayParams gp{};
-    std::memcpy(gp.dT16, hl.dT16, sizeof(gp.dT16));
     gp.n = n;
     gp.m = pl.m;
     gp.nh = pl.nh;
@@ -339,7 +359,6 @@ bf_status bf_low_spectrum(const void* J, const void* h, int n, int S, bf_dtype d
     gp.ntasks = 1ull << pl.nh;
     gp.S = S;
     gp.list_cap = L.list_cap;
-    gp.W = hl.W;
     gp.seg_log2 = pl.seg_log2;
     gp.inner_bits = pl.inner_bits;
     gp.spill_cap = L.spill_cap;
@@ -370,7 +389,6 @@ bf_status bf_low_spectrum(const void* J, const void* h, int n, int S, bf_dtype d
         tp.ntasks = 1ull << pl.nh;
         tp.S = S;
         tp.list_cap = L.list_cap;
-        tp.W = hl.W;
         tp.seg_log2 = pl.seg_log2;
         tp.spill_cap = L.spill_cap;
         // split residuals <= 2^-18 |x| for 8 values below 2^30, FP32 accumulation and conversions
@@ -393,17 +411,22 @@ bf_status bf_low_spectrum(const void* J, const void* h, int n, int S, bf_dtype d
         g_prof.valid = true;
     }
 
-    e = bf::launch_absorb_spill(AE, AC, pl.grid, L.list_cap, S, hl.W, gp.spill_E, gp.spill_C, L.spill_cap, hdr, stream);
+    e = bf::launch_absorb_spill(AE, AC, pl.grid, L.list_cap, S, 0, gp.spill_E, gp.spill_C, L.spill_cap, hdr, stream,
+                                Wd);
     if (e != cudaSuccess) return cuda_fail(e, "spill absorb");
-    e = merge_tree(AE, AC, BE, BC, pl.grid, L.list_cap, S, hl.W, hdr, stream, in_a);
+    e = merge_tree(AE, AC, BE, BC, pl.grid, L.list_cap, S, 0, hdr, stream, in_a, Wd);
     if (e != cudaSuccess) return cuda_fail(e, "merge rounds");
     const int* FE = in_a ? AE : BE;
     const unsigned long long* FC = in_a ? AC : BC;
-    e = bf::launch_finalize(FE, FC, L.list_cap, S, n, dtype, hl.q, J, h, reinterpret_cast<double*>(ws + L.rescore),
-                            energies, out_states, hdr, stream);
+    e = bf::launch_finalize(FE, FC, L.list_cap, S, n, dtype, 0, J, h, reinterpret_cast<double*>(ws + L.rescore),
+                            energies, out_states, hdr, stream, qd);
     if (e != cudaSuccess) return cuda_fail(e, "finalize");
     return BF_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 bf_status bf_workspace_status(const void* workspace, void* stream_ptr)
 {
@@ -450,18 +473,15 @@ bf_status bf_low_spectrum_qubo(const void* a, const void* b, int n, int S, bf_dt
     if (e == cudaSuccess)
         e = bf::launch_qubo_prep(a, b, n, (int)dtype, ws + q.J, ws + q.h, ws + q.off, flag, stream);
     if (e != cudaSuccess) return cuda_fail(e, "QUBO map");
-    if (dtype == BF_I32) {
-        unsigned hflag = 0;
-        e = cudaMemcpyAsync(&hflag, flag, sizeof(hflag), cudaMemcpyDeviceToHost, stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-        if (e != cudaSuccess) return cuda_fail(e, "QUBO map status");
-        if (hflag) return fail(BF_EUNSUPPORTED, "2 b_i + sum_j a_ij outside int32: use a float dtype");
-    }
+    // integer inputs whose 2 b_i + sum_j a_ij leaves int32 set the flag; preparation turns it into
+    // the out-of-range status (BF_EUNSUPPORTED from bf_workspace_status) and nothing is walked
     const bf_dtype inner_dt = dtype == BF_I32 ? BF_I32 : BF_F64;
-    st = bf_low_spectrum(ws + q.J, ws + q.h, n, S, inner_dt, F, states, workspace, q.inner, opt, stream_ptr);
+    st = low_spectrum_impl(ws + q.J, ws + q.h, n, S, inner_dt, F, states, workspace, q.inner, opt, stream_ptr,
+                           flag);
     if (st != BF_OK) return st;
     auto* hdr = reinterpret_cast<bf::WsHeader*>(ws);
-    e = bf::launch_qubo_finish(F, S, dtype == BF_I32 ? 0 : 1, ws + q.off, &hdr->status, stream);
+    e = bf::launch_qubo_finish(F, S, dtype == BF_I32 ? 0 : 1, ws + q.off, &hdr->status, stream,
+                               dtype == BF_I32 ? flag : nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "QUBO offset");
     return BF_OK;
 }

@@ -62,8 +62,8 @@ struct alignas(16) WsHeader {
 };
 static_assert(sizeof(WsHeader) == 256, "header size");
 
-// Per-instance constants produced by the preparation kernel.  The leading
-// part (PrepLaunch) is copied to the host and becomes kernel parameters.
+// Per-instance constants produced by the preparation kernel and read on the device by the
+// kernels after it (the increments dT16 through a constant table, see GrayParams).
 struct PrepLaunch {
     int status;           // kErr* bits found during preparation
     int q;                // fixed-point scale exponent
@@ -151,13 +151,16 @@ __host__ inline Layout make_layout(int S, int max_blocks, int spill_log2)
 
 // ---- kernel parameter blocks -------------------------------------------
 
+// The packed 16-bit pair-energy increments of the unrolled walk (Prep::L.dT16) are read by
+// gray_kernel from a __constant__ table that launch_gray fills from the workspace with a
+// stream-ordered device-to-device copy; the candidate window W comes from the workspace too,
+// so no host synchronisation sits between preparation and enumeration.
 struct GrayParams {
-    unsigned dT16[kGrayMaxInnerSteps]; // index t = 1..2^inner_bits - 1; entry 0 unused
     int n, m, nh;                   // spins, walked middle spins, task-index bits
     int free_bits;
     unsigned long long hiconst;     // fixed top bits of every configuration
     unsigned long long ntasks;      // 2^nh
-    int S, list_cap, W, seg_log2;
+    int S, list_cap, seg_log2;
     unsigned spill_cap;
     int inner_bits;                 // spins of the unrolled block (9 or 10)
     const Prep* prep;
@@ -175,14 +178,15 @@ struct PrepParams {
     unsigned long long hiconst;
     int emq_log2;                   // |E_q| and |local fields| < 2^emq_log2
     int inner_bits;                 // inner spins of the Gray walk the tables are built for
+    const unsigned* range_flag;     // optional: nonzero *range_flag marks the instance out of range
     Prep* prep;
     WsHeader* hdr;
 };
 
-struct TcParams {                   // tensor-core screening kernel (k_tc.cu)
+struct TcParams {                   // tensor-core screening kernel (k_tc.cu); W is read from prep
     int n, m, nh, free_bits;        // m walked outer spins per task, nh task-index bits
     unsigned long long hiconst, ntasks;
-    int S, list_cap, W, seg_log2;
+    int S, list_cap, seg_log2;
     unsigned spill_cap;
     int delta;                      // widening of the tensor-core test (quantised units)
     int stall_test;                 // testing only: the MMA warps issue nothing (bounded waits run out)
@@ -328,18 +332,21 @@ size_t gray_smem_bytes(int n, int list_cap);
 
 // Merge of sorted record lists: `nin` lists of `cap` records each in
 // (inE, inC) are merged pairwise into ceil(nin / 2) lists in (outE, outC).
+// Wp != nullptr: the window is read on the device from *Wp instead of W.
 cudaError_t launch_merge_round(const int* inE, const unsigned long long* inC, int nin,
                                int* outE, unsigned long long* outC, int cap, int S, int W,
-                               WsHeader* hdr, cudaStream_t s);
+                               WsHeader* hdr, cudaStream_t s, const int* Wp = nullptr);
 // Fold the spill area into the `nlists` lists of (E, C) (grid-stride over chunks).
 cudaError_t launch_absorb_spill(int* E, unsigned long long* C, int nlists, int cap, int S, int W,
                                 const int* spill_E, const unsigned long long* spill_C,
-                                unsigned spill_cap, WsHeader* hdr, cudaStream_t s);
+                                unsigned spill_cap, WsHeader* hdr, cudaStream_t s, const int* Wp = nullptr);
 // Final selection: integer instances write E_q >> q; float instances
 // re-evaluate Eq. (1) in FP64 from the caller's J, h and reselect.
+// qp != nullptr: the scale exponent is read on the device from *qp instead of q.
 cudaError_t launch_finalize(const int* E, const unsigned long long* C, int cap, int S, int n, int dtype,
                             int q, const void* J, const void* h, double* rescore,
-                            void* energies, unsigned long long* states, WsHeader* hdr, cudaStream_t s);
+                            void* energies, unsigned long long* states, WsHeader* hdr, cudaStream_t s,
+                            const int* qp = nullptr);
 // Seed: `blocks` lists of the lowest sampled records (sample configurations in total).
 cudaError_t launch_seed(const Prep* prep, int n, int free_bits, unsigned long long hiconst,
                         unsigned long long sample, int per_block, int blocks, int cap, int* outE,
@@ -358,7 +365,9 @@ cudaError_t launch_set_tau(const int* E, int S, WsHeader* hdr, cudaStream_t s);
 // (double out and offset for both)
 cudaError_t launch_qubo_prep(const void* a, const void* b, int n, int dtype, void* Jout, void* hout, void* off4,
                              unsigned* flag, cudaStream_t s);
-cudaError_t launch_qubo_finish(void* F, int S, int dtype, const void* off4, unsigned* flag, cudaStream_t s);
+// map_flag (optional, integer form): nonzero marks the search out of range in *flag (the status word)
+cudaError_t launch_qubo_finish(void* F, int S, int dtype, const void* off4, unsigned* flag, cudaStream_t s,
+                               const unsigned* map_flag = nullptr);
 // Two-state Potts model as an Ising instance (k_qubo.cu): J' = J, h'_i = h_i(1) - h_i(0),
 // C = sum_{i<j} J_ij + sum_i (h_i(0) + h_i(1)); energies E = (E' + C) / 2 (same dtypes as the QUBO map)
 cudaError_t launch_potts2_prep(const void* J, const void* h, int n, int dtype, void* Jout, void* hout, void* cst,

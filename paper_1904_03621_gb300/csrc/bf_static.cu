@@ -12,7 +12,8 @@
 // library holds its 4 MiB until the process exits.  Host code cannot use
 // the symbol's name as a device address, so the first call on each device
 // (with that device current) asks the runtime for the address once and
-// caches it.  Calls share the array: two calls whose work overlaps on the
+// caches it for the life of the process (a cudaDeviceReset() destroys the
+// array with its context, after which this entry point must not be called).  Calls share the array: two calls whose work overlaps on the
 // GPU (different streams, or the same device from several host threads
 // without ordering) race on it and give undefined results.
 #include <cstring>

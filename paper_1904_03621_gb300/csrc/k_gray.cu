@@ -34,6 +34,8 @@
 // into its sorted list of the lowest records, tightens its threshold and
 // publishes it with atomicMin; blocks read the global threshold back.
 #include <climits>
+#include <cstddef>
+#include <mutex>
 #include <utility>
 
 #include "bf_internal.cuh"
@@ -44,6 +46,10 @@ namespace {
 
 constexpr int kVarBits = 10;   // task-index bits that differ within one batch of tasks
 static_assert(kGrayThreads * kWalks == 1 << kVarBits, "a batch is 2^kVarBits tasks");
+
+// packed 16-bit pair-energy increments of the unrolled steps (Prep::L.dT16 of the search being
+// run), copied in by launch_gray; read as constant-bank operands of the step additions
+__constant__ unsigned c_dT16[kGrayMaxInnerSteps];
 
 __host__ __device__ constexpr int cx_ctz(int t) { return (t & 1) ? 0 : 1 + cx_ctz(t >> 1); }
 // value (1 = +1) of the spin flipped by step t of the reflected Gray code
@@ -56,19 +62,19 @@ struct Packed {
 };
 
 template <int IB, int t>
-__device__ __forceinline__ void inner_step(Packed<IB>& w, const GrayParams& p)
+__device__ __forceinline__ void inner_step(Packed<IB>& w)
 {
     constexpr int k = cx_ctz(t);
     constexpr bool up = cx_up(t);
-    w.Xa += (up ? w.Ga[k] : 0u - w.Ga[k]) + p.dT16[t];
-    w.Xb += (up ? w.Gb[k] : 0u - w.Gb[k]) + p.dT16[t];
+    w.Xa += (up ? w.Ga[k] : 0u - w.Ga[k]) + c_dT16[t];
+    w.Xb += (up ? w.Gb[k] : 0u - w.Gb[k]) + c_dT16[t];
     w.M = __vminu2(__vminu2(w.M, w.Xa), w.Xb);
 }
 
 template <int IB, int... Ts>
-__device__ __forceinline__ void inner_walk(Packed<IB>& w, const GrayParams& p, std::integer_sequence<int, Ts...>)
+__device__ __forceinline__ void inner_walk(Packed<IB>& w, std::integer_sequence<int, Ts...>)
 {
-    (inner_step<IB, Ts + 1>(w, p), ...);
+    (inner_step<IB, Ts + 1>(w), ...);
 }
 
 // integer packing hi * 2^16 + lo of the 16-bit views (floor(x / 2^16)) of two int32 values
@@ -175,6 +181,14 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const Prep* prep = p.prep;
+    if (*(volatile unsigned*)&p.hdr->status & kErrRange) {
+        // the instance is outside the fixed-point range (reported by the workspace status): no walk
+        for (int i = tid; i < cap; i += blockDim.x) {
+            p.list_E[(size_t)blockIdx.x * cap + i] = kEmptyE;
+            p.list_C[(size_t)blockIdx.x * cap + i] = kEmptyC;
+        }
+        return;
+    }
     for (int i = tid; i < n * n; i += blockDim.x) s.Jq[i] = prep->Jq[i];
     for (int i = tid; i < kMaxN; i += blockDim.x) s.hq[i] = prep->hq[i];
     for (int i = tid; i < IS; i += blockDim.x) s.T[i] = prep->T[i];
@@ -187,7 +201,7 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
     }
     __syncthreads();
 
-    const int S = p.S, W = p.W, m = p.m;
+    const int S = p.S, W = prep->L.W, m = p.m;
     const int walk_shift = IB + m;       // task index sits above inner + middle spins
     const unsigned nblocks = 1u << m;
     const unsigned seg_mask = (1u << p.seg_log2) - 1u;
@@ -387,7 +401,7 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
             pk.Xa = pack_energy(E0[0], E0[1]);
             pk.Xb = pack_energy(E0[2], E0[3]);
             pk.M = __vminu2(pk.Xa, pk.Xb);
-            inner_walk<IB>(pk, p, std::make_integer_sequence<int, IS - 1>{});
+            inner_walk<IB>(pk, std::make_integer_sequence<int, IS - 1>{});
             const bool flag_lo = (pk.M & 0xffffu) <= thr16;
             const bool flag_hi = (pk.M >> 16) <= thr16;
             if (__any_sync(0xffffffffu, flag_lo || flag_hi)) {
@@ -546,9 +560,43 @@ cudaError_t launch_gray_ib(const GrayParams& p, int grid, cudaStream_t s)
     return cudaGetLastError();
 }
 
+namespace {
+
+// The increment table is one per device.  Searches on different streams are ordered through
+// it: a launch waits for the previous enumeration kernel on this device (an event recorded
+// after it) before overwriting the table.  Inside a stream capture that event cannot be
+// waited on, so a captured search relies on the order of the graph's launches instead.
+constexpr int kMaxDevices = 64;
+std::mutex g_table_mutex;
+cudaEvent_t g_table_free[kMaxDevices];
+
+}  // namespace
+
 cudaError_t launch_gray(const GrayParams& p, int grid, cudaStream_t s)
 {
-    return p.inner_bits == 10 ? launch_gray_ib<10>(p, grid, s) : launch_gray_ib<9>(p, grid, s);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
+    const bool ordered = cs == cudaStreamCaptureStatusNone;
+    std::lock_guard<std::mutex> lock(g_table_mutex);
+    if (ordered) {
+        if (!g_table_free[dev]) {
+            e = cudaEventCreateWithFlags(&g_table_free[dev], cudaEventDisableTiming);
+            if (e != cudaSuccess) return e;
+        }
+        e = cudaStreamWaitEvent(s, g_table_free[dev], 0);
+        if (e != cudaSuccess) return e;
+    }
+    const void* table = reinterpret_cast<const char*>(p.prep) + offsetof(Prep, L) + offsetof(PrepLaunch, dT16);
+    e = cudaMemcpyToSymbolAsync(c_dT16, table, sizeof(c_dT16), 0, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    e = p.inner_bits == 10 ? launch_gray_ib<10>(p, grid, s) : launch_gray_ib<9>(p, grid, s);
+    if (e != cudaSuccess) return e;
+    return ordered ? cudaEventRecord(g_table_free[dev], s) : cudaSuccess;
 }
 
 }  // namespace bf

@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(const PrepParams p)
     }
     if (tid == 0) {
         int status = s_status;
+        if (p.range_flag && *p.range_flag) status |= kErrRange;   // found by the caller's own map
         int W = 0;
         if (p.dtype != 0 && s_delta > 0.0) {
             // candidates must cover 2 delta (quantisation, both directions) plus the FP64

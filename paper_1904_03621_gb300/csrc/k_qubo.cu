@@ -111,9 +111,11 @@ __global__ void potts2_finish_f64_kernel(double* E, int S, const double* cst)
 }
 
 // F[k] = (E'[k] + off4) / 4
-__global__ void qubo_finish_i64_kernel(long long* F, int S, const long long* off4, unsigned* flag)
+__global__ void qubo_finish_i64_kernel(long long* F, int S, const long long* off4, unsigned* flag,
+                                       const unsigned* map_flag)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0 && map_flag && *map_flag) atomicOr(flag, kErrRange);   // h' left int32: the search was void
     if (k >= S) return;
     const long long v = F[k] + *off4;
     if (v & 3ll) atomicOr(flag, 2u);       // cannot happen for a consistent instance
@@ -179,12 +181,13 @@ cudaError_t launch_potts2_finish(void* E, int S, int dtype, const void* cst, uns
     return cudaGetLastError();
 }
 
-cudaError_t launch_qubo_finish(void* F, int S, int dtype, const void* off4, unsigned* flag, cudaStream_t s)
+cudaError_t launch_qubo_finish(void* F, int S, int dtype, const void* off4, unsigned* flag, cudaStream_t s,
+                               const unsigned* map_flag)
 {
     const int blocks = (S + 255) / 256;
     if (dtype == 0)
         qubo_finish_i64_kernel<<<blocks, 256, 0, s>>>(static_cast<long long*>(F), S,
-                                                      static_cast<const long long*>(off4), flag);
+                                                      static_cast<const long long*>(off4), flag, map_flag);
     else
         qubo_finish_f64_kernel<<<blocks, 256, 0, s>>>(static_cast<double*>(F), S, static_cast<const double*>(off4));
     count_launches(1);

@@ -42,8 +42,9 @@ __device__ int keep_count(const int* E, int len, int valid, int S, int W, int ca
 
 __global__ void __launch_bounds__(kMergeThreads) merge_kernel(const int* inE, const unsigned long long* inC, int nin,
                                                               int* outE, unsigned long long* outC, int cap, int S,
-                                                              int W, WsHeader* hdr)
+                                                              int W, WsHeader* hdr, const int* Wp)
 {
+    if (Wp) W = *Wp;
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long* C = reinterpret_cast<unsigned long long*>(smem);
     int* E = reinterpret_cast<int*>(C + 2 * cap);
@@ -71,8 +72,9 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(const int* inE, co
 __global__ void __launch_bounds__(kMergeThreads) absorb_kernel(int* LE, unsigned long long* LC, int nlists, int cap,
                                                                int S, int W, const int* spE,
                                                                const unsigned long long* spC, unsigned spill_cap,
-                                                               WsHeader* hdr)
+                                                               WsHeader* hdr, const int* Wp)
 {
+    if (Wp) W = *Wp;
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long* C = reinterpret_cast<unsigned long long*>(smem);
     int* E = reinterpret_cast<int*>(C + 2 * cap);
@@ -110,8 +112,10 @@ __global__ void __launch_bounds__(kMergeThreads) absorb_kernel(int* LE, unsigned
 // ---- final selection -------------------------------------------------------
 
 __global__ void __launch_bounds__(256) finalize_int_kernel(const int* E, const unsigned long long* C, int S, int q,
-                                                           long long* energies, unsigned long long* states)
+                                                           const int* qp, long long* energies,
+                                                           unsigned long long* states)
 {
+    if (qp) q = *qp;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < S; k += gridDim.x * blockDim.x) {
         energies[k] = (long long)(E[k] >> q);   // E_q = E * 2^q exactly for integer instances
         states[k] = C[k];
@@ -172,35 +176,36 @@ __global__ void __launch_bounds__(kMergeThreads) finalize_float_kernel(const uns
 }  // namespace
 
 cudaError_t launch_merge_round(const int* inE, const unsigned long long* inC, int nin, int* outE,
-                               unsigned long long* outC, int cap, int S, int W, WsHeader* hdr, cudaStream_t s)
+                               unsigned long long* outC, int cap, int S, int W, WsHeader* hdr, cudaStream_t s,
+                               const int* Wp)
 {
     size_t smem = (size_t)2 * cap * 12;
     cudaError_t e = cudaFuncSetAttribute(merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    merge_kernel<<<(nin + 1) / 2, kMergeThreads, smem, s>>>(inE, inC, nin, outE, outC, cap, S, W, hdr);
+    merge_kernel<<<(nin + 1) / 2, kMergeThreads, smem, s>>>(inE, inC, nin, outE, outC, cap, S, W, hdr, Wp);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_absorb_spill(int* E, unsigned long long* C, int nlists, int cap, int S, int W, const int* spill_E,
                                 const unsigned long long* spill_C, unsigned spill_cap, WsHeader* hdr,
-                                cudaStream_t s)
+                                cudaStream_t s, const int* Wp)
 {
     size_t smem = (size_t)2 * cap * 12;
     cudaError_t e = cudaFuncSetAttribute(absorb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    absorb_kernel<<<nlists, kMergeThreads, smem, s>>>(E, C, nlists, cap, S, W, spill_E, spill_C, spill_cap, hdr);
+    absorb_kernel<<<nlists, kMergeThreads, smem, s>>>(E, C, nlists, cap, S, W, spill_E, spill_C, spill_cap, hdr, Wp);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(const int* E, const unsigned long long* C, int cap, int S, int n, int dtype, int q,
                             const void* J, const void* h, double* rescore, void* energies,
-                            unsigned long long* states, WsHeader* hdr, cudaStream_t s)
+                            unsigned long long* states, WsHeader* hdr, cudaStream_t s, const int* qp)
 {
     (void)hdr;
     if (dtype == 0) {
-        finalize_int_kernel<<<(S + 255) / 256, 256, 0, s>>>(E, C, S, q, static_cast<long long*>(energies), states);
+        finalize_int_kernel<<<(S + 255) / 256, 256, 0, s>>>(E, C, S, q, qp, static_cast<long long*>(energies), states);
         count_launches(1);
         return cudaGetLastError();
     }

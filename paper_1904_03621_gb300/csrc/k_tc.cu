@@ -240,6 +240,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const Prep* prep = p.prep;
+    if (*(volatile unsigned*)&p.hdr->status & kErrRange) {
+        // the instance is outside the fixed-point range (reported by the workspace status): no walk
+        for (int i = tid; i < cap; i += blockDim.x) {
+            p.list_E[(size_t)blockIdx.x * cap + i] = kEmptyE;
+            p.list_C[(size_t)blockIdx.x * cap + i] = kEmptyC;
+        }
+        return;
+    }
 
     for (int i = tid; i < n * n; i += blockDim.x) s.Jq[i] = prep->Jq[i];
     for (int i = tid; i < kMaxN; i += blockDim.x) s.hq[i] = prep->hq[i];
@@ -304,7 +312,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const __grid_constant
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = s_tmem;
 
-    const int S = p.S, W = p.W;
+    const int S = p.S, W = prep->L.W;
     const int walk_shift = kTcSpins + m;
     const unsigned ntiles = 1u << m;
     const unsigned seg_mask = (1u << p.seg_log2) - 1u;

@@ -4,6 +4,7 @@ Every value written here comes from ``oracle`` (the CPU reference) applied to
 instances from ``paper_1904_03621_gb300.instances``; nothing comes from the
 CUDA library.  Usage (from the repository root):
 
+    python tests/golden/make_golden.py plain_n20        # full 2^20 enumeration, S=10
     python tests/golden/make_golden.py int_n32          # full 2^32 enumeration, S=100
     python tests/golden/make_golden.py float_n48_sub    # 64 fixed-prefix subspaces of 2^24, S=1000
     python tests/golden/make_golden.py batched_sample   # 96 sampled instances of the 4096 batch, S=10
@@ -77,6 +78,17 @@ def read(path):
     return {b: (np.array(v[0]), np.array(v[1], dtype=np.uint64)) for b, v in out.items()}
 
 
+def make_plain_n20():
+    o = oracle.get()
+    J, h = instances.plain_n20()
+    t = time.time()
+    en, st = o.low_spectrum(J, h, 10)
+    dt = time.time() - t
+    _write(os.path.join(HERE, "plain_n20_S10.txt.gz"),
+           ["instance plain_n20 seed 0 (n=20, J_ij~N(0,1), h_i~N(0,1), FP64), S=10, full enumeration",
+            f"oracle {dt:.1f} s on {o.num_threads} threads"], [(0, (en, st))])
+
+
 def make_int_n32():
     o = oracle.get()
     J, h = instances.int_n32()
@@ -132,7 +144,7 @@ def make_grad_sample():
 
 
 if __name__ == "__main__":
-    jobs = {"int_n32": make_int_n32, "float_n48_sub": make_float_n48_sub,
+    jobs = {"plain_n20": make_plain_n20, "int_n32": make_int_n32, "float_n48_sub": make_float_n48_sub,
             "batched_sample": make_batched_sample, "grad_sample": make_grad_sample}
     for name in sys.argv[1:]:
         jobs[name]()

@@ -87,3 +87,23 @@ def test_noalloc_rejects_searches_beyond_its_array(env):
     assert b"4 MiB" in _lib.load().bf_last_error_detail()
     status, _, _ = _noalloc(torch, _lib, Jt, ht, 1 << 25)
     assert status == _lib.BF_EINVAL
+
+
+def test_noalloc_reports_device_status_then_recovers(env):
+    """A flood of equal energies into a 16-record spill area must come back from this entry point
+    as BF_EOVERFLOW (it waits for its work and returns the device-side status), and the next call
+    on the shared array, which still holds that error word, must succeed and match bf_low_spectrum."""
+    torch, _lib, api = env
+    n = 20
+    Jz = torch.zeros(n, n, dtype=torch.int32, device="cuda")
+    hz = torch.zeros(n, dtype=torch.int32, device="cuda")
+    status, _, _ = _noalloc(torch, _lib, Jz, hz, 10, _lib.Options(spill_log2=4))
+    assert status == _lib.BF_EOVERFLOW, _lib.load().bf_last_error_detail().decode()
+    J, h = instances.dense_pm1(22, 8)
+    Jt = torch.from_numpy(np.ascontiguousarray(J)).cuda()
+    ht = torch.from_numpy(np.ascontiguousarray(h)).cuda()
+    en_ref, st_ref = api.low_spectrum(Jt, ht, 50)
+    status, en, st = _noalloc(torch, _lib, Jt, ht, 50)
+    assert status == _lib.BF_OK, _lib.load().bf_last_error_detail().decode()
+    assert np.array_equal(en.cpu().numpy(), en_ref.cpu().numpy())
+    assert np.array_equal(api.states_u64(st), api.states_u64(st_ref))
