@@ -55,7 +55,7 @@ REF_STEP_FREE_BITS = 22        # reference arm: one subspace of 2^22 configurati
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one gray_kernel launch on the
 # float_n48 workload, from one ncu capture of that launch.  Reported only while the kernel's
 # sources (k_gray.cu, bf_sort.cuh and the GrayParams block) hash to what they were then.
-GRAY_TRAFFIC = {"workload": "float_n48", "bytes": 1062400, "sources_sha256_16": "af3aa71afd31ab4a"}
+GRAY_TRAFFIC = {"workload": "float_n48", "bytes": 1764864, "sources_sha256_16": "804b231ef0544c4e"}
 
 
 def gray_sources_hash() -> str:
@@ -663,6 +663,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--variant", default="gray", choices=["gray", "tc"],
                     help="screening kernel: Gray-code walk or tensor-core tiles")
+    ap.add_argument("--inner-bits", type=int, default=0, choices=[0, 9, 10],
+                    help="spins of the unrolled block of the Gray walk (0 = library default)")
     ap.add_argument("--fig3", action="store_true",
                     help="time-to-solution sweep over N (the paper's Fig. 3) instead of the benchmark line")
     ap.add_argument("--fig3-max-n", type=int, default=50)
@@ -714,8 +716,8 @@ def main():
     hh = torch.from_numpy(np.ascontiguousarray(h)).pin_memory()
     Jd = torch.empty_like(Jh, device=dev)
     hd = torch.empty_like(hh, device=dev)
-    ws = torch.empty(api.workspace_size(n, S, Jh.dtype, variant={"gray": 1, "tc": 2}[args.variant]),
-                     dtype=torch.uint8, device=dev)
+    ws = torch.empty(api.workspace_size(n, S, Jh.dtype, variant={"gray": 1, "tc": 2}[args.variant],
+                                        inner_bits=args.inner_bits), dtype=torch.uint8, device=dev)
     edt = torch.int64 if Jh.dtype == torch.int32 else torch.float64
     en = torch.empty(S, dtype=edt, device=dev)
     st = torch.empty(S, dtype=torch.int64, device=dev)
@@ -731,7 +733,8 @@ def main():
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        api.low_spectrum(Jd, hd, S, workspace=ws, out=(en, st), check=False, profile=profile, variant=variant)
+        api.low_spectrum(Jd, hd, S, workspace=ws, out=(en, st), check=False, profile=profile, variant=variant,
+                         inner_bits=args.inner_bits)
         ev1.record(stream)
         en_h.copy_(en, non_blocking=True)
         st_h.copy_(st, non_blocking=True)
@@ -792,7 +795,8 @@ def main():
                           "kernel_ms": gray_ms / args.steps, "kernel_share_of_step": gray_ms / dev_ms}
     else:
         achieved = ALU_OPS_PER_CONFIG * configs_per_step / gray_s
-        roofline_block = {"bound": "alu", "kernel": "gray_kernel<10>", "achieved": achieved / 1e9,
+        inner = args.inner_bits or (10 if n >= 42 else 9)
+        roofline_block = {"bound": "alu", "kernel": f"gray_kernel<{inner}>", "achieved": achieved / 1e9,
                           "peak": peak_ops / 1e9, "unit": "Gop/s", "frac": achieved / peak_ops,
                           "traffic": gray_traffic(args.workload),
                           "ops_per_config": ALU_OPS_PER_CONFIG,
