@@ -208,7 +208,7 @@ size_t bf_batched_workspace_size(int B, int n_max, int S, bf_dtype dtype, const 
  *   energies   device out, B x S row-major: int64 for BF_I32, double otherwise
  *   states     device out, B x S configuration integers
  *   workspace  device, >= bf_batched_workspace_size(...) bytes, 256-byte aligned
- * opt->task_log2 sets log2 of the configurations per work unit (default 22),
+ * opt->task_log2 sets log2 of the configurations per work unit (default 25),
  * opt->grid_blocks the persistent grid.  No host synchronisation and no
  * allocation: the call is capturable in a CUDA graph.  Instances with n out
  * of range are reported by bf_workspace_status as BF_EINVAL (their output

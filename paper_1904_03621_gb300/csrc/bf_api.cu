@@ -781,9 +781,10 @@ bf_status make_bplan(int B, int n_max, int S, int dtype, const bf_options* opt, 
     bp.n_max = n_max;
     bp.S = S;
     bp.dtype = dtype;
-    // a work unit is 2^10 walks of 2^(9+m) configurations: 2^(19+m) per unit
-    bp.m_cap = o.task_log2 ? std::min(std::max(o.task_log2 - 19, 0), 16) : 6;
-    const int ubits = std::max(0, n_max - 19 - bp.m_cap);
+    // a work unit is 2^10 walks of 2^(kBWalkBits + m) configurations: 2^(kBWalkBits + 10 + m) per unit
+    constexpr int kUnitBase = bf::kBWalkBits + 10;
+    bp.m_cap = std::min(std::max((o.task_log2 ? o.task_log2 : 25) - kUnitBase, 0), 16);
+    const int ubits = std::max(0, n_max - kUnitBase - bp.m_cap);
     const long long units_max = 1ll << ubits;
     long long pool = units_max * S + 512;
     if (pool > 8192) pool = 8192;
@@ -952,7 +953,7 @@ extern "C" bf_status bf_autotune_batched(int B, const void* J_packed, const int6
     float best_t = 1e30f;
     bf_options best_o{};
     int tried = 0;
-    const int task_candidates[] = {21, 23, 25, 27};
+    const int task_candidates[] = {21, 22, 23, 24, 25, 26, 27};
     for (int tl : task_candidates) {
         for (int per_sm = 1; per_sm <= bps; per_sm++) {
             bf_options o{};

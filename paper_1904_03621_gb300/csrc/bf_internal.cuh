@@ -21,8 +21,10 @@
 namespace bf {
 
 constexpr int kMaxN = 64;
-constexpr int kInnerBits = 9;                    // spins walked inside one unrolled block (batched walker)
-constexpr int kInnerSteps = 1 << kInnerBits;     // configurations per block and walk (batched walker)
+constexpr int kInnerBits = 9;                    // spins of the batched preparation's seed walks
+constexpr int kInnerSteps = 1 << kInnerBits;     // configurations per seed walk
+constexpr int kBWalkBits = 9;                    // spins walked inside one unrolled block (batched walker)
+constexpr int kBWalkSteps = 1 << kBWalkBits;     // configurations per block and walk (batched walker)
 constexpr int kGrayMaxInnerBits = 10;            // the same for the single-instance Gray walk (9 or 10)
 constexpr int kGrayMaxInnerSteps = 1 << kGrayMaxInnerBits;
 constexpr int kGrayLargeFreeBits = 42;           // searches of >= 2^42 configurations use 10 inner spins
@@ -285,8 +287,8 @@ struct BInst {                                   // per-instance constants (devi
     double delta, emax;
     int Jq[kBMaxN * kBMaxN];
     int hq[kBMaxN];
-    int T[kInnerSteps];
-    unsigned dT16[kInnerSteps];
+    int T[kBWalkSteps];                          // inner pair energies of the walker's block
+    unsigned dT16[kBWalkSteps];
     int col[kBMaxN][16];
 };
 

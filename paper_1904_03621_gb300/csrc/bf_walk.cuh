@@ -1,6 +1,6 @@
 // Primitives of the Gray-code walk shared by the enumeration kernels.
 //
-// Reflected Gray code over the kInnerBits inner spins: step t (1 .. 2^kInnerBits - 1)
+// Reflected Gray code over the IB inner spins: step t (1 .. 2^IB - 1)
 // flips spin ctz(t) to the value of that bit in gray(t) = t ^ (t >> 1).  The 16-bit
 // view of an int32 energy or field is floor(x / 2^16); two walks share one
 // 32-bit register as the integer hi * 2^16 + lo, so one 32-bit add advances
@@ -34,9 +34,10 @@ __device__ __forceinline__ unsigned threshold16(int tau)
     return th > 0xffffu ? 0xffffu : th;
 }
 
+template <int IB>
 struct Packed {
     unsigned Xa, Xb, M;
-    unsigned Ga[kInnerBits], Gb[kInnerBits];
+    unsigned Ga[IB], Gb[IB];
 };
 
 }  // namespace bf

@@ -34,15 +34,16 @@ namespace {
 constexpr int kBWarps = 8;                    // warps per block of the walker
 constexpr int kBThreads = kBWarps * 32;
 constexpr int kBUnitWalkBits = 10;            // a work unit: 2^10 walks (256 threads x 4)
-constexpr int kBBuf = 2 * kInnerSteps;       // records per warp buffer (room for one walk's rescan)
+constexpr int kBBuf = 1024;                  // records per warp buffer (merged before a 32-record chunk could overflow it)
+constexpr int kBKeepMax = kBBuf / 2;         // records a merged buffer may keep (S plus the float window)
 constexpr int kBSeed = 1024;                  // sampled configurations per instance for its first threshold
 constexpr int kBSeedThreads = 256;
 constexpr int kBDescents = 2;                 // local searches per warp of the preparation block
 constexpr unsigned long long kBDescentSalt = 0x13198A2E03707344ull;
 constexpr size_t kBWarpSmem = (size_t)kBBuf * 12;                 // record buffer bytes per warp
 constexpr int kBSyncEvery = 1;                   // unrolled blocks between block barriers
-// + the unit's tables: dT16, T (kInnerSteps each), J_q (kBMaxN^2), h_q (kBMaxN), columns (kBMaxN x 16)
-constexpr size_t kBSmem = kBWarpSmem * kBWarps + (size_t)kInnerSteps * 8 + (size_t)kBMaxN * kBMaxN * 4 +
+// + the unit's tables: dT16, T (kBWalkSteps each), J_q (kBMaxN^2), h_q (kBMaxN), columns (kBMaxN x 16)
+constexpr size_t kBSmem = kBWarpSmem * kBWarps + (size_t)kBWalkSteps * 8 + (size_t)kBMaxN * kBMaxN * 4 +
                           (size_t)kBMaxN * 4 + (size_t)kBMaxN * 16 * 4;
 
 __device__ __forceinline__ double load_value(const void* p, int dtype, size_t idx)
@@ -130,6 +131,7 @@ __global__ void __launch_bounds__(kBSeedThreads, 2) bprep_kernel(const BatchPara
     __shared__ int hq[kBMaxN];
     __shared__ int Tq[kInnerSteps];
     __shared__ __align__(16) int dTx[kInnerSteps];   // exact T[gray(t)] - T[gray(t-1)]
+    __shared__ int Tw[kBWalkSteps];                  // the walker's inner pair energies (10 spins)
     __shared__ int sE[kBSeed];
     __shared__ unsigned long long sC[kBSeed];
     __shared__ int s_q, s_status, s_tau, s_dE[kBSeedThreads / 32], s_F[kBMaxN];
@@ -207,6 +209,15 @@ __global__ void __launch_bounds__(kBSeedThreads, 2) bprep_kernel(const BatchPara
             for (int k = i + 1; k < kInnerBits; k++) t += Jq[i * n + k] * si * (((g >> k) & 1) ? 1 : -1);
         }
         Tq[g] = t;
+    }
+    static_assert(kBWalkBits <= kBMinN, "the walker's inner spins exist in every instance");
+    for (int g = tid; g < kBWalkSteps; g += blockDim.x) {
+        int t = 0;
+        for (int i = 0; i < kBWalkBits; i++) {
+            int si = ((g >> i) & 1) ? 1 : -1;
+            for (int k = i + 1; k < kBWalkBits; k++) t += Jq[i * n + k] * si * (((g >> k) & 1) ? 1 : -1);
+        }
+        Tw[g] = t;
     }
     __syncthreads();
     for (int s = tid; s < kInnerSteps; s += blockDim.x) {
@@ -373,18 +384,18 @@ __global__ void __launch_bounds__(kBSeedThreads, 2) bprep_kernel(const BatchPara
     // outputs
     for (int idx = tid; idx < n * n; idx += blockDim.x) I->Jq[idx] = Jq[idx];
     for (int i = tid; i < kBMaxN; i += blockDim.x) I->hq[i] = i < n ? hq[i] : 0;
-    for (int g = tid; g < kInnerSteps; g += blockDim.x) {
-        I->T[g] = Tq[g];
+    for (int g = tid; g < kBWalkSteps; g += blockDim.x) {
+        I->T[g] = Tw[g];
         unsigned v = 0;
         if (g > 0) {
             int g1 = g ^ (g >> 1), g0 = (g - 1) ^ ((g - 1) >> 1);
-            v = (unsigned)((Tq[g1] >> 16) - (Tq[g0] >> 16)) * 65537u;
+            v = (unsigned)((Tw[g1] >> 16) - (Tw[g0] >> 16)) * 65537u;
         }
         I->dT16[g] = v;
     }
     for (int idx = tid; idx < kBMaxN * 16; idx += blockDim.x) {
         int j = idx / 16, k = idx % 16;
-        int row = k < kInnerBits + kKeep ? k : -1;
+        int row = k < kBWalkBits + kKeep ? k : -1;
         I->col[j][k] = (j < n && row >= 0 && row < n) ? Jq[row * n + j] : 0;
     }
     if (tid == 0) {
@@ -396,9 +407,9 @@ __global__ void __launch_bounds__(kBSeedThreads, 2) bprep_kernel(const BatchPara
             if (w > (double)(1 << 28)) { w = (double)(1 << 28); status |= kErrRange; }
             W = (int)w;
         }
-        int m = n - kInnerBits - kBUnitWalkBits;   // 2^10 tasks per unit
+        int m = n - kBWalkBits - kBUnitWalkBits;   // 2^10 tasks per unit
         m = m < 0 ? 0 : (m > p.m_cap ? p.m_cap : m);
-        const int nh = n - kInnerBits - m;
+        const int nh = n - kBWalkBits - m;
         I->n = n;
         I->q = q;
         I->W = W;
@@ -507,8 +518,8 @@ __device__ int warp_merge(int* E, unsigned long long* C, int count, int S, int W
         long long lim = (long long)kE + W;
         keep = upper_bound_key(E, len, lim > INT_MAX - 1 ? INT_MAX - 1 : (int)lim);
         if (keep > count) keep = count;
-        if (keep > kBBuf - kInnerSteps) {
-            keep = kBBuf - kInnerSteps;
+        if (keep > kBKeepMax) {
+            keep = kBKeepMax;
             if (lane == 0) atomicOr(status, kErrWindow);
         }
     }
@@ -516,7 +527,7 @@ __device__ int warp_merge(int* E, unsigned long long* C, int count, int S, int W
 }
 
 template <int t>
-__device__ __forceinline__ void bstep(Packed& w, unsigned d)
+__device__ __forceinline__ void bstep(Packed<kBWalkBits>& w, unsigned d)
 {
     if constexpr (t > 0) {
         constexpr int k = cx_ctz(t);
@@ -529,7 +540,7 @@ __device__ __forceinline__ void bstep(Packed& w, unsigned d)
 
 // four steps per 128-bit shared-memory load of the instance's increments
 template <int g>
-__device__ __forceinline__ void bwalk_group(Packed& w, const uint4* tab4)
+__device__ __forceinline__ void bwalk_group(Packed<kBWalkBits>& w, const uint4* tab4)
 {
     const uint4 d = tab4[g];
     bstep<4 * g + 0>(w, d.x);
@@ -539,7 +550,7 @@ __device__ __forceinline__ void bwalk_group(Packed& w, const uint4* tab4)
 }
 
 template <int... Gs>
-__device__ __forceinline__ void bwalk_block(Packed& w, const uint4* tab4, std::integer_sequence<int, Gs...>)
+__device__ __forceinline__ void bwalk_block(Packed<kBWalkBits>& w, const uint4* tab4, std::integer_sequence<int, Gs...>)
 {
     (bwalk_group<Gs>(w, tab4), ...);
 }
@@ -550,18 +561,19 @@ __device__ __forceinline__ void bwalk_block(Packed& w, const uint4* tab4, std::i
 
 __global__ void __launch_bounds__(kBThreads, 2) bwalk_kernel(const BatchParams p)
 {
-    // dynamic shared memory: per warp C[kBBuf], E[kBBuf]; then the unit's dT16[kInnerSteps], T[kInnerSteps]
+    // dynamic shared memory: per warp C[kBBuf], E[kBBuf]; then the unit's dT16[kBWalkSteps], T[kBWalkSteps]
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned long long* Cw = reinterpret_cast<unsigned long long*>(smem_raw + (size_t)wid * kBWarpSmem);
     int* Ew = reinterpret_cast<int*>(Cw + kBBuf);
     unsigned* dTw = reinterpret_cast<unsigned*>(smem_raw + kBWarpSmem * kBWarps);
-    int* Tw = reinterpret_cast<int*>(dTw + kInnerSteps);
-    int* Jq = Tw + kInnerSteps;                       // n x n (row stride n)
+    int* Tw = reinterpret_cast<int*>(dTw + kBWalkSteps);
+    int* Jq = Tw + kBWalkSteps;                       // n x n (row stride n)
     int* hq = Jq + kBMaxN * kBMaxN;
     int (*colq)[16] = reinterpret_cast<int(*)[16]>(hq + kBMaxN);
     __shared__ unsigned long long s_unit;
     __shared__ int s_count[kBWarps];
+    __shared__ int s_g[kBWarps][kBWalkBits];          // field row of the walk a warp is rescanning
     const unsigned long long total = *(volatile unsigned long long*)&p.hdr->total_units;
     const int S = p.S;
 
@@ -582,7 +594,7 @@ __global__ void __launch_bounds__(kBThreads, 2) bwalk_kernel(const BatchParams p
         const BInst* I = p.inst + b;
         const int n = I->n, m = I->m, W = I->W;
         const unsigned long long ntasks = 1ull << I->nh;
-        for (int i = threadIdx.x; i < kInnerSteps; i += blockDim.x) {
+        for (int i = threadIdx.x; i < kBWalkSteps; i += blockDim.x) {
             dTw[i] = I->dT16[i];
             Tw[i] = I->T[i];
         }
@@ -592,10 +604,10 @@ __global__ void __launch_bounds__(kBThreads, 2) bwalk_kernel(const BatchParams p
         __syncthreads();
 
         // walks of this thread: tasks lu * 2^10 + threadIdx.x * 4 + w
-        int E0[kWalks], G[kWalks][kInnerBits], Fm[kWalks][kKeep];
+        int E0[kWalks], G[kWalks][kBWalkBits], Fm[kWalks][kKeep];
         unsigned long long cfg0[kWalks];
         unsigned active_mask = 0;
-        const int walk_shift = kInnerBits + m;
+        const int walk_shift = kBWalkBits + m;
         const unsigned long long task0 = (lu << kBUnitWalkBits) + (unsigned long long)(threadIdx.x * kWalks);
 #pragma unroll
         for (int w = 0; w < kWalks; w++)
@@ -613,14 +625,14 @@ __global__ void __launch_bounds__(kBThreads, 2) bwalk_kernel(const BatchParams p
             }
             E0[0] = e;
 #pragma unroll
-            for (int k = 0; k < kInnerBits; k++) {
+            for (int k = 0; k < kBWalkBits; k++) {
                 int f = hq[k];
-                for (int j = kInnerBits; j < n; j++) f += ((c >> j) & 1ull) ? Jq[k * n + j] : -Jq[k * n + j];
+                for (int j = kBWalkBits; j < n; j++) f += ((c >> j) & 1ull) ? Jq[k * n + j] : -Jq[k * n + j];
                 G[0][k] = 2 * f;
             }
 #pragma unroll
             for (int r = 0; r < kKeep; r++) {
-                const int l = kInnerBits + r;
+                const int l = kBWalkBits + r;
                 int f = l < n ? hq[l] : 0;
                 if (l < n)
                     for (int j = 0; j < n; j++) f += ((c >> j) & 1ull) ? Jq[l * n + j] : -Jq[l * n + j];
@@ -636,7 +648,7 @@ __global__ void __launch_bounds__(kBThreads, 2) bwalk_kernel(const BatchParams p
             cfg0[w] = ((active_mask >> w) & 1u) ? (cfg0[from] ^ (1ull << j)) : cfg0[from];
             E0[w] = E0[from];
 #pragma unroll
-            for (int k = 0; k < kInnerBits; k++) G[w][k] = G[from][k];
+            for (int k = 0; k < kBWalkBits; k++) G[w][k] = G[from][k];
 #pragma unroll
             for (int r = 0; r < kKeep; r++) Fm[w][r] = Fm[from][r];
             if (j < n && (active_mask >> w) & 1u) {
@@ -647,21 +659,21 @@ __global__ void __launch_bounds__(kBThreads, 2) bwalk_kernel(const BatchParams p
                 const unsigned dE = (unsigned)f << 1;
                 E0[w] = (int)((unsigned)E0[w] + (up ? dE : 0u - dE));
 #pragma unroll
-                for (int k = 0; k < kInnerBits; k++) {
+                for (int k = 0; k < kBWalkBits; k++) {
                     const unsigned d = (unsigned)Jq[k * n + j] << 2;
                     G[w][k] = (int)((unsigned)G[w][k] + (up ? d : 0u - d));
                 }
 #pragma unroll
                 for (int r = 0; r < kKeep; r++) {
-                    const int l = kInnerBits + r;
+                    const int l = kBWalkBits + r;
                     const unsigned d = l < n ? (unsigned)Jq[l * n + j] << 1 : 0u;
                     Fm[w][r] = (int)((unsigned)Fm[w][r] + (up ? d : 0u - d));
                 }
             }
         }
-        Packed pk;
+        Packed<kBWalkBits> pk;
 #pragma unroll
-        for (int k = 0; k < kInnerBits; k++) {
+        for (int k = 0; k < kBWalkBits; k++) {
             pk.Ga[k] = pack_hi16(G[0][k], G[1][k]);
             pk.Gb[k] = pack_hi16(G[2][k], G[3][k]);
         }
@@ -671,10 +683,12 @@ __global__ void __launch_bounds__(kBThreads, 2) bwalk_kernel(const BatchParams p
         unsigned long long kC = kEmptyC;
         int tau_scr = 0;
         unsigned thr16 = 0;
-        // tg: the instance threshold as read from global memory (it only decreases, so a value
-        // read earlier is still a valid bound)
+        // tg: the instance threshold as read from global memory.  It only decreases, so every
+        // value read is a valid bound and the lowest one read so far is the tightest.
+        int tg_low = INT_MAX;
         auto refresh_with = [&](int tg) {
-            int t = min(tg, kE);
+            tg_low = min(tg_low, tg);
+            int t = min(tg_low, kE);
             long long ts = (long long)t + W;
             tau_scr = (int)(ts > (1ll << 30) ? (1ll << 30) : ts);
             thr16 = threshold16(tau_scr);
@@ -692,7 +706,7 @@ __global__ void __launch_bounds__(kBThreads, 2) bwalk_kernel(const BatchParams p
             pk.Xa = pack_energy(E0[0], E0[1]);
             pk.Xb = pack_energy(E0[2], E0[3]);
             pk.M = __vminu2(pk.Xa, pk.Xb);
-            bwalk_block(pk, reinterpret_cast<const uint4*>(dTw), std::make_integer_sequence<int, kInnerSteps / 4>{});
+            bwalk_block(pk, reinterpret_cast<const uint4*>(dTw), std::make_integer_sequence<int, kBWalkSteps / 4>{});
             const unsigned flags = (((pk.M & 0xffffu) <= thr16) ? 1u : 0u) | (((pk.M >> 16) <= thr16) ? 2u : 0u);
             const unsigned bal = __ballot_sync(0xffffffffu, flags != 0u);
             if (bal) {
@@ -705,25 +719,37 @@ __global__ void __launch_bounds__(kBThreads, 2) bwalk_kernel(const BatchParams p
                     for (int w = 0; w < kWalks; w++) {
                         if (!((fL >> (w & 1)) & 1u) || !((aL >> w) & 1u)) continue;
                         const int e0 = __shfl_sync(0xffffffffu, E0[w], L);
-                        int g8[kInnerBits];
+                        if (lane == L) {
 #pragma unroll
-                        for (int k = 0; k < kInnerBits; k++) g8[k] = __shfl_sync(0xffffffffu, G[w][k], L);
-                        const unsigned long long cb = __shfl_sync(0xffffffffu, cfg0[w], L) | cmid;
-                        if (count > kBBuf - kInnerSteps) {
-                            count = warp_merge(Ew, Cw, count, S, W, kE, kC, &p.hdr->status, lane);
-                            if (count >= S && lane == 0) atomicMin(&p.tau[b], kE);
-                            __syncwarp();
-                            refresh();
+                            for (int k = 0; k < kBWalkBits; k++) s_g[wid][k] = G[w][k];
                         }
+                        const unsigned long long cb = __shfl_sync(0xffffffffu, cfg0[w], L) | cmid;
+                        __syncwarp();
+                        // lane l walks Gray steps t = l R .. l R + R - 1 of the block: it sums the fields of
+                        // its first configuration, then follows one flip per step
+                        constexpr unsigned R = kBWalkSteps / 32;
+                        const int* Gs = s_g[wid];
                         const unsigned base_e = (unsigned)e0 - (unsigned)Tw[0];
+                        unsigned t = (unsigned)lane * R;
+                        unsigned g = t ^ (t >> 1);
+                        unsigned sg = 0u;
 #pragma unroll
-                        for (int j = 0; j < kInnerSteps / 32; j++) {
-                            const int t = j * 32 + lane;
-                            const int g = t ^ (t >> 1);
-                            unsigned acc = base_e + (unsigned)Tw[g];
-#pragma unroll
-                            for (int k = 0; k < kInnerBits; k++) acc += ((g >> k) & 1) ? (unsigned)g8[k] : 0u;
-                            const int e = (int)acc;
+                        for (int k = 0; k < kBWalkBits; k++) sg += ((g >> k) & 1u) ? (unsigned)Gs[k] : 0u;
+#pragma unroll 4
+                        for (unsigned i = 0; i < R; i++) {
+                            if (count > kBBuf - 32) {
+                                // room for the next 32 records: merge first (count is warp-uniform)
+                                count = warp_merge(Ew, Cw, count, S, W, kE, kC, &p.hdr->status, lane);
+                                if (count >= S && lane == 0) atomicMin(&p.tau[b], kE);
+                                __syncwarp();
+                                refresh();
+                            }
+                            if (i > 0) {
+                                const int k = __ffs(++t) - 1;
+                                g ^= 1u << k;
+                                sg += ((g >> k) & 1u) ? (unsigned)Gs[k] : 0u - (unsigned)Gs[k];
+                            }
+                            const int e = (int)(base_e + (unsigned)Tw[g] + sg);
                             const unsigned long long c = cb | (unsigned long long)g;
                             const bool hit = e <= tau_scr && !(W == 0 && e == kE && c > kC);
                             const unsigned hb = __ballot_sync(0xffffffffu, hit);
@@ -751,7 +777,7 @@ __global__ void __launch_bounds__(kBThreads, 2) bwalk_kernel(const BatchParams p
             if (ub + 1 < nblocks) {
                 const unsigned u1 = ub + 1;
                 const int jrel = __ffs(u1) - 1;
-                const int j = kInnerBits + jrel;
+                const int j = kBWalkBits + jrel;
                 const bool up = ((u1 ^ (u1 >> 1)) >> jrel) & 1u;
                 int F[kWalks];
                 if (jrel < kKeep) {
@@ -771,27 +797,27 @@ __global__ void __launch_bounds__(kBThreads, 2) bwalk_kernel(const BatchParams p
                         F[w] = f;
                     }
                 }
-                int colv[kInnerBits + kKeep];
+                int colv[kBWalkBits + kKeep];
 #pragma unroll
-                for (int k = 0; k < kInnerBits + kKeep; k++) colv[k] = colq[j][k];
+                for (int k = 0; k < kBWalkBits + kKeep; k++) colv[k] = colq[j][k];
 #pragma unroll
                 for (int w = 0; w < kWalks; w++) {
                     const unsigned dE = (unsigned)F[w] << 1;
                     E0[w] = (int)((unsigned)E0[w] + (up ? dE : 0u - dE));
 #pragma unroll
-                    for (int k = 0; k < kInnerBits; k++) {
+                    for (int k = 0; k < kBWalkBits; k++) {
                         const unsigned d = (unsigned)colv[k] << 2;
                         G[w][k] = (int)((unsigned)G[w][k] + (up ? d : 0u - d));
                     }
 #pragma unroll
                     for (int r = 0; r < kKeep; r++) {
-                        const unsigned d = (unsigned)colv[kInnerBits + r] << 1;
+                        const unsigned d = (unsigned)colv[kBWalkBits + r] << 1;
                         Fm[w][r] = (int)((unsigned)Fm[w][r] + (up ? d : 0u - d));
                     }
                 }
                 cmid ^= 1ull << j;
 #pragma unroll
-                for (int k = 0; k < kInnerBits; k++) {
+                for (int k = 0; k < kBWalkBits; k++) {
                     pk.Ga[k] = pack_hi16(G[0][k], G[1][k]);
                     pk.Gb[k] = pack_hi16(G[2][k], G[3][k]);
                 }
@@ -809,14 +835,14 @@ __global__ void __launch_bounds__(kBThreads, 2) bwalk_kernel(const BatchParams p
             for (int w2 = 1; w2 < kBWarps; w2++) {
                 const int cw = s_count[w2];
                 if (cw == 0) continue;
-                if (count > kBBuf - kInnerSteps) {
+                if (count + cw > kBBuf) {
                     count = warp_merge(Ew, Cw, count, S, W, kE, kC, &p.hdr->status, lane);
                     __syncwarp();
                 }
                 const unsigned long long* C2 =
                     reinterpret_cast<const unsigned long long*>(smem_raw + (size_t)w2 * kBWarpSmem);
                 const int* E2 = reinterpret_cast<const int*>(C2 + kBBuf);
-                for (int i = lane; i < cw; i += 32) {   // cw <= kBBuf - kInnerSteps: fits
+                for (int i = lane; i < cw; i += 32) {   // count, cw <= kBKeepMax after the merges: fits
                     Ew[count + i] = E2[i];
                     Cw[count + i] = C2[i];
                 }
