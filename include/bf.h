@@ -95,10 +95,11 @@ typedef enum {
  *                workspace status is BF_ETIMEOUT.  The CUDA context stays
  *                usable.  Ignored by the other kernels.
  *   inner_bits   spins walked by the fully unrolled block of the Gray-code walk:
- *                0 = automatic (the autotuned choice for this device and search
- *                size, else 10 for searches of at least 2^42 configurations and
- *                9 below), or 9 or 10 (10 needs n >= 14).  Results do not depend
- *                on it.  Ignored by the tensor-core variant.
+ *                0 = automatic (10 for searches of at least 2^42 configurations
+ *                and 9 below), or 9 or 10 (10 needs n >= 14).  Results do not
+ *                depend on it.  Ignored by the tensor-core variant.
+ * When variant, inner_bits, task_log2 and grid_blocks are all 0 and bf_autotune
+ * has run for this device and (n, n - fixed_bits, S, dtype), its choice is used.
  */
 typedef struct {
     int32_t variant;
@@ -150,6 +151,42 @@ bf_status bf_low_spectrum(const void* J, const void* h, int n, int S, bf_dtype d
                           void* energies, uint64_t* states,
                           void* workspace, size_t workspace_bytes,
                           const bf_options* opt, void* stream);
+
+/*
+ * bf_autotune -- choose the screening kernel and launch shape of bf_low_spectrum
+ * for one search size by timing candidates on this GPU (CUDA events on
+ * `stream`), as the paper chooses its launch configuration by measurement
+ * (Sec. 4.2).  Candidates: the Gray-code walk with 9 and 10 inner spins, the
+ * default task length (task_log2) and lengths 2^2 and 2^4 shorter and 2^2
+ * longer (at most 2^14 blocks per task), 1 or 2 blocks per SM; the
+ * tensor-core variant with three task lengths where n - fixed_bits >= 15.  Each candidate runs bf_low_spectrum's
+ * plan on J, h (arguments as for bf_low_spectrum; `base` supplies fixed_bits,
+ * fixed_value and spill_log2, may be NULL).  Searches of more than 2^39
+ * configurations time only the end of the task queue: at least 2^39
+ * configurations and two batches of tasks per block (same task shape as the
+ * full search), starting from the threshold an untimed run of the same part
+ * reached, as most of a full search runs near its final threshold; a full
+ * n = 48 tuning takes a few seconds.  Smaller searches run whole.  Candidates whose workspace exceeds
+ * workspace_bytes are skipped (bf_workspace_size with default options fits
+ * them all).  Writes the fastest options to *best (fixed_bits / fixed_value
+ * as given) and, if best_rate is not NULL, its configurations per second, and
+ * caches the choice for this device and (n, n - fixed_bits, S, dtype): later
+ * bf_low_spectrum / bf_workspace_size calls that leave variant, inner_bits,
+ * task_log2 and grid_blocks at 0 use it.  Results never depend on the choice.
+ * If records is not NULL, up to records_cap candidates and their rates are
+ * written there and *records_count (may be NULL) receives their number.
+ * Synchronises the stream; energies / states / workspace hold no result
+ * afterwards.
+ */
+typedef struct {
+    bf_options opt;           /* a candidate */
+    double configs_per_s;     /* its measured rate (0 if it did not run: workspace, overflow) */
+} bf_tune_record;
+
+bf_status bf_autotune(const void* J, const void* h, int n, int S, bf_dtype dtype, void* energies, uint64_t* states,
+                      void* workspace, size_t workspace_bytes, const bf_options* base, void* stream,
+                      bf_options* best, double* best_rate, bf_tune_record* records, int records_cap,
+                      int* records_count);
 
 /*
  * bf_low_spectrum_noalloc -- bf_low_spectrum for callers that cannot

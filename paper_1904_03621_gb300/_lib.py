@@ -15,7 +15,7 @@ BF_I32, BF_F32, BF_F64 = 0, 1, 2
 BF_VARIANT_AUTO, BF_VARIANT_GRAY, BF_VARIANT_TC = 0, 1, 2
 
 # every symbol include/bf.h declares
-EXPORTS = ["bf_workspace_size", "bf_low_spectrum", "bf_low_spectrum_noalloc", "bf_batched_workspace_size",
+EXPORTS = ["bf_workspace_size", "bf_low_spectrum", "bf_autotune", "bf_low_spectrum_noalloc", "bf_batched_workspace_size",
            "bf_low_spectrum_batched", "bf_autotune_batched", "bf_low_spectrum_backward", "bf_qubo_workspace_size",
            "bf_low_spectrum_qubo", "bf_potts_workspace_size", "bf_low_spectrum_potts", "bf_instance_digest", "bf_cursor_bytes", "bf_cursor_init",
            "bf_cursor_workspace_size", "bf_cursor_step", "bf_cursor_state", "bf_workspace_status",
@@ -29,6 +29,10 @@ class Options(ctypes.Structure):
                 ("task_log2", ctypes.c_int32), ("grid_blocks", ctypes.c_int32), ("spill_log2", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("stall_test", ctypes.c_int32), ("inner_bits", ctypes.c_int32),
                 ("reserved", ctypes.c_int32 * 4)]
+
+
+class TuneRecord(ctypes.Structure):
+    _fields_ = [("opt", Options), ("configs_per_s", ctypes.c_double)]
 
 
 class IssueRates(ctypes.Structure):
@@ -62,6 +66,10 @@ def load(path: str | None = None):
     lib.bf_workspace_size.argtypes = [i32, i32, i32, ctypes.POINTER(Options)]
     lib.bf_low_spectrum.restype = i32
     lib.bf_low_spectrum.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, sz, ctypes.POINTER(Options), vp]
+    lib.bf_autotune.restype = i32
+    lib.bf_autotune.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, sz, ctypes.POINTER(Options), vp,
+                                ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(TuneRecord),
+                                i32, ctypes.POINTER(ctypes.c_int)]
     lib.bf_low_spectrum_noalloc.restype = i32
     lib.bf_low_spectrum_noalloc.argtypes = [vp, vp, i32, i32, i32, vp, vp, ctypes.POINTER(Options), vp]
     lib.bf_batched_workspace_size.restype = sz

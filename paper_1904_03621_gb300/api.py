@@ -81,6 +81,49 @@ def low_spectrum(J: torch.Tensor, h: torch.Tensor, S: int, *, variant: int = 0, 
     return energies, states
 
 
+def autotune(J: torch.Tensor, h: torch.Tensor, S: int, *, fixed_bits: int = 0, fixed_value: int = 0,
+             spill_log2: int = 0, stream=None) -> dict:
+    """Time the candidate kernels and launch shapes of low_spectrum for this search size (bf_autotune).
+
+    Returns {"variant", "inner_bits", "task_log2", "grid_blocks", "configs_per_s", "candidates"}
+    (every candidate with its measured rate); the choice is cached in the library for this device
+    and (n, n - fixed_bits, S, dtype), so later calls that leave variant, inner_bits, task_log2 and
+    grid_blocks at 0 use it.
+    """
+    lib = _lib.load()
+    if J.dtype not in _DTYPES or h.dtype != J.dtype:
+        raise TypeError("J and h must share one of int32, float32, float64")
+    n = J.shape[0]
+    J = J.contiguous()
+    h = h.contiguous()
+    base = _options(0, fixed_bits, fixed_value, 0, 0, spill_log2)
+    nbytes = lib.bf_workspace_size(n, S, _DTYPES[J.dtype], ctypes.byref(_options(1, fixed_bits, fixed_value, 0, 0,
+                                                                                   spill_log2)))
+    if nbytes == 0:
+        raise _lib.BFError(_lib.BF_EINVAL, lib.bf_last_error_detail().decode())
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=J.device)
+    edt = torch.int64 if J.dtype == torch.int32 else torch.float64
+    en = torch.empty(S, dtype=edt, device=J.device)
+    st = torch.empty(S, dtype=torch.int64, device=J.device)
+    best = _lib.Options()
+    rate = ctypes.c_double(0.0)
+    recs = (_lib.TuneRecord * 64)()
+    count = ctypes.c_int(0)
+    _lib.check(lib.bf_autotune(J.data_ptr(), h.data_ptr(), n, S, _DTYPES[J.dtype], en.data_ptr(), st.data_ptr(),
+                               ws.data_ptr(), nbytes, ctypes.byref(base), _stream_handle(stream), ctypes.byref(best),
+                               ctypes.byref(rate), recs, 64, ctypes.byref(count)), lib)
+
+    def brief(o):
+        return {"variant": o.variant, "inner_bits": o.inner_bits, "task_log2": o.task_log2,
+                "grid_blocks": o.grid_blocks}
+
+    out = brief(best)
+    out["configs_per_s"] = float(rate.value)
+    out["candidates"] = [dict(brief(recs[i].opt), configs_per_s=float(recs[i].configs_per_s))
+                         for i in range(count.value)]
+    return out
+
+
 def low_spectrum_qubo(a: torch.Tensor, b: torch.Tensor, S: int, *, variant: int = 0, fixed_bits: int = 0,
                       fixed_value: int = 0, task_log2: int = 0, grid_blocks: int = 0, spill_log2: int = 0,
                       stream=None, workspace: torch.Tensor | None = None, check: bool = True):

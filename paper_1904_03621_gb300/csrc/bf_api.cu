@@ -88,6 +88,26 @@ int ceil_log2(unsigned long long x)
     return k;
 }
 
+// autotuned options per (device, n, n - fixed_bits, S, dtype), written by bf_autotune and used
+// by make_plan when the caller leaves variant, inner_bits, task_log2 and grid_blocks at 0
+using SingleKey = std::tuple<int, int, int, int, int>;
+std::mutex g_single_mutex;
+std::map<SingleKey, bf_options> g_single_cache;
+
+void apply_single_tune(int n, int S, int dtype, bf_options& o)
+{
+    if (o.variant || o.inner_bits || o.task_log2 || o.grid_blocks) return;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    std::lock_guard<std::mutex> lock(g_single_mutex);
+    auto it = g_single_cache.find(SingleKey{dev, n, n - o.fixed_bits, S, dtype});
+    if (it == g_single_cache.end()) return;
+    o.variant = it->second.variant;
+    o.inner_bits = it->second.inner_bits;
+    o.task_log2 = it->second.task_log2;
+    o.grid_blocks = it->second.grid_blocks;
+}
+
 struct Plan {
     int n, S, dtype, free_bits;
     unsigned long long hiconst;
@@ -104,6 +124,7 @@ bf_status make_plan(int n, int S, int dtype, const bf_options* opt, Plan& pl)
 {
     bf_options o{};
     if (opt) o = *opt;
+    apply_single_tune(n, S, dtype, o);
     if (n < 1 || n > bf::kMaxN) return fail(BF_EINVAL, "n=%d outside [1, 64]", n);
     if (dtype != BF_I32 && dtype != BF_F32 && dtype != BF_F64) return fail(BF_EINVAL, "unknown dtype %d", dtype);
     if (o.variant != BF_VARIANT_AUTO && o.variant != BF_VARIANT_GRAY && o.variant != BF_VARIANT_TC)
@@ -248,9 +269,14 @@ bf_status report(bf_status s, const char* detail) { return fail(s, "%s", detail)
 }  // namespace bf
 
 namespace {
+// tune_configs > 0 (autotuner only): the enumeration kernel takes only the last tasks of its
+// queue, about tune_configs configurations; *walked receives their number.  tune_tau: a
+// threshold known from an earlier run on the same instance (quantised units), which the walk
+// starts from, as the later tasks of a full search do
 bf_status low_spectrum_impl(const void* J, const void* h, int n, int S, bf_dtype dtype, void* energies,
                             uint64_t* states, void* workspace, size_t workspace_bytes, const bf_options* opt,
-                            void* stream_ptr, const unsigned* range_flag);
+                            void* stream_ptr, const unsigned* range_flag, unsigned long long tune_configs = 0,
+                            double* walked = nullptr, int tune_tau = 0x7fffffff);
 }  // namespace
 
 extern "C" {
@@ -278,12 +304,14 @@ namespace {
 // instance as out of range (the QUBO map's int32 check), without a host round trip
 bf_status low_spectrum_impl(const void* J, const void* h, int n, int S, bf_dtype dtype, void* energies,
                             uint64_t* states, void* workspace, size_t workspace_bytes, const bf_options* opt,
-                            void* stream_ptr, const unsigned* range_flag)
+                            void* stream_ptr, const unsigned* range_flag, unsigned long long tune_configs,
+                            double* walked, int tune_tau)
 {
     g_detail.clear();
     Plan pl;
     bf_status st = make_plan(n, S, dtype, opt, pl);
     if (st != BF_OK) return st;
+    if (walked) *walked = (double)(1ull << pl.free_bits);
     if (!J || !h || !energies || !states || !workspace) return fail(BF_EINVAL, "null pointer argument");
     if (workspace_bytes < pl.bytes)
         return fail(BF_EWORKSPACE, "workspace of %zu bytes < %zu required", workspace_bytes, pl.bytes);
@@ -368,6 +396,26 @@ bf_status low_spectrum_impl(const void* J, const void* h, int n, int S, bf_dtype
     gp.list_C = AC;
     gp.spill_E = reinterpret_cast<int*>(ws + L.spill_E);
     gp.spill_C = reinterpret_cast<unsigned long long*>(ws + L.spill_C);
+    if (tune_configs) {
+        // autotuner: start the task counter near the end of the queue, so that the kernel walks
+        // about tune_configs configurations with the full search's task shape
+        const int task_bits = (pl.variant == BF_VARIANT_TC ? 15 : pl.inner_bits) + pl.m;
+        const unsigned long long ntasks = 1ull << pl.nh;
+        const unsigned long long gran = pl.variant == BF_VARIANT_TC ? 1ull : (unsigned long long)bf::kGrayThreads * bf::kWalks;
+        // at least two batches of tasks per block, so that every block works as in the full search
+        unsigned long long want = std::max((tune_configs >> task_bits) + 1, 2ull * (unsigned long long)pl.grid * gran);
+        want = (want + gran - 1) / gran * gran;
+        if (want < ntasks) {
+            const unsigned long long start = ntasks - want;
+            e = cudaMemcpyAsync(&hdr->task_next, &start, sizeof(start), cudaMemcpyHostToDevice, stream);
+            if (e != cudaSuccess) return cuda_fail(e, "task counter");
+            if (walked) *walked = (double)want * (double)(1ull << task_bits);
+        }
+        if (tune_tau != 0x7fffffff) {
+            e = bf::launch_tau_min(hdr, tune_tau, stream);
+            if (e != cudaSuccess) return cuda_fail(e, "tuning threshold");
+        }
+    }
     const bool profile = opt && opt->profile;
     if (profile) {
         if (!g_prof.start) {
@@ -928,6 +976,150 @@ extern "C" bf_status bf_merge_lists(int k, const void* const* energies, const ui
         w++;
     }
     if (w < S) return fail(BF_EINVAL, "only %d distinct records for S=%d", w, S);
+    return BF_OK;
+}
+
+// ---- autotuner for the single-instance search -------------------------------------
+
+extern "C" bf_status bf_autotune(const void* J, const void* h, int n, int S, bf_dtype dtype, void* energies,
+                                 uint64_t* states, void* workspace, size_t workspace_bytes, const bf_options* base,
+                                 void* stream_ptr, bf_options* best, double* best_rate, bf_tune_record* records,
+                                 int records_cap, int* records_count)
+{
+    g_detail.clear();
+    if (!best) return fail(BF_EINVAL, "null output options");
+    if (records_count) *records_count = 0;
+    bf_options b0{};
+    if (base) b0 = *base;
+    b0.variant = 0;
+    b0.inner_bits = 0;
+    b0.task_log2 = 0;
+    b0.grid_blocks = 0;
+    b0.profile = 0;
+    b0.stall_test = 0;
+    Plan pl0;
+    {
+        bf_options probe = b0;
+        probe.variant = BF_VARIANT_GRAY;           // not the cache: validate the arguments as given
+        bf_status st = make_plan(n, S, dtype, &probe, pl0);
+        if (st != BF_OK) return st;
+    }
+    if (!J || !h || !energies || !states || !workspace) return fail(BF_EINVAL, "null pointer argument");
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "device query");
+
+    // candidates: the Gray walk with 9 and 10 inner spins, the default task length and two
+    // either side of it, 1 or 2 blocks per SM; the tensor-core variant where it applies
+    std::vector<bf_options> cand;
+    if (!pl0.direct) {
+        const int bps = bf::gray_blocks_per_sm(bf::list_capacity(S));
+        for (int ib : {9, 10}) {
+            if (ib == 10 && n < 10 + bf::kKeep) continue;
+            bf_options o = b0;
+            o.variant = BF_VARIANT_GRAY;
+            o.inner_bits = ib;
+            Plan p;
+            if (make_plan(n, S, dtype, &o, p) != BF_OK) continue;
+            const int walk_bits = pl0.free_bits - ib;
+            for (int dm : {0, -2, 2, -4}) {
+                const int m = p.m + dm;
+                if (dm != 0 && (m < 0 || m > std::min(walk_bits, 14))) continue;
+                for (int per_sm = 1; per_sm <= std::max(bps, 1); per_sm++) {
+                    bf_options c = o;
+                    c.task_log2 = ib + m;
+                    c.grid_blocks = sms * per_sm;
+                    cand.push_back(c);
+                }
+            }
+        }
+        if (pl0.free_bits >= 15) {
+            bf_options o = b0;
+            o.variant = BF_VARIANT_TC;
+            Plan p;
+            if (make_plan(n, S, dtype, &o, p) == BF_OK) {
+                for (int dm : {0, -2, 2}) {
+                    const int m = p.m + dm;
+                    if (m < 0 || m > std::min(pl0.free_bits - 15, 16)) continue;
+                    bf_options c = o;
+                    c.task_log2 = 15 + m;
+                    cand.push_back(c);
+                }
+            }
+        }
+    } else {
+        cand.push_back(b0);                          // tiny space: one kernel, nothing to choose
+    }
+
+    cudaEvent_t t0, t1;
+    if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess)
+        return fail(BF_ECUDA, "event creation failed");
+    // searches beyond 2^39 configurations time the last 2^39 of the task queue
+    const unsigned long long tune_configs = pl0.free_bits > 39 ? (1ull << 39) : 0ull;
+    double best_r = -1.0;
+    bf_options best_o = cand.front();
+    int tried = 0;
+    int nrec = 0;
+    auto note = [&](const bf_options& c, double rate) {
+        if (records && nrec < records_cap) {
+            records[nrec].opt = c;
+            records[nrec].configs_per_s = rate;
+            nrec++;
+            if (records_count) *records_count = nrec;
+        }
+    };
+    for (const bf_options& c : cand) {
+        Plan p;
+        if (make_plan(n, S, dtype, &c, p) != BF_OK || p.bytes > workspace_bytes) { note(c, 0.0); continue; }
+        double configs = 0.0;
+        bf_status st = BF_OK;
+        float ms = 0.f;
+        int tau_ref = 0x7fffffff;
+        for (int rep = 0; rep < 2 && st == BF_OK; rep++) {       // one untimed run, then one timed run
+            if (rep == 1 && tune_configs) {
+                // the timed part of the queue starts from the threshold the untimed run reached, as
+                // the bulk of a full search runs with a threshold close to its final S-th energy
+                const auto* hdr = static_cast<const bf::WsHeader*>(workspace);
+                e = cudaMemcpyAsync(&tau_ref, &hdr->tau, sizeof(int), cudaMemcpyDeviceToHost, stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+                if (e != cudaSuccess) st = cuda_fail(e, "tuning threshold");
+            }
+            if (st == BF_OK && rep == 1 && cudaEventRecord(t0, stream) != cudaSuccess) st = fail(BF_ECUDA, "event record");
+            if (st == BF_OK)
+                st = low_spectrum_impl(J, h, n, S, dtype, energies, states, workspace, workspace_bytes, &c, stream_ptr,
+                                       nullptr, tune_configs, &configs, tau_ref);
+        }
+        if (st == BF_OK) {
+            e = cudaEventRecord(t1, stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+            if (e != cudaSuccess) st = cuda_fail(e, "autotune timing");
+        }
+        if (st != BF_OK && st != BF_EUNSUPPORTED) {
+            cudaEventDestroy(t0);
+            cudaEventDestroy(t1);
+            return st;
+        }
+        if (st != BF_OK) { note(c, 0.0); continue; }
+        // a truncated run leaves partial lists: only its time counts.  Device conditions of a
+        // full run (overflow) disqualify the candidate.
+        if (!tune_configs && bf_workspace_status(workspace, stream_ptr) != BF_OK) { note(c, 0.0); continue; }
+        const double rate = configs / (ms * 1e-3);
+        note(c, rate);
+        tried++;
+        if (rate > best_r) { best_r = rate; best_o = c; }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (!tried) return fail(BF_EWORKSPACE, "no candidate fits the workspace of %zu bytes", workspace_bytes);
+    best_o.fixed_bits = b0.fixed_bits;
+    best_o.fixed_value = b0.fixed_value;
+    *best = best_o;
+    if (best_rate) *best_rate = best_r;
+    std::lock_guard<std::mutex> lock(g_single_mutex);
+    g_single_cache[SingleKey{dev, n, pl0.free_bits, S, (int)dtype}] = best_o;
     return BF_OK;
 }
 

@@ -362,6 +362,8 @@ cudaError_t launch_descent_seed(const Prep* prep, int n, int free_bits, unsigned
                                 cudaStream_t s);
 // hdr->tau = E[S - 1] of a merged list; resets the task and spill counters.
 cudaError_t launch_set_tau(const int* E, int S, WsHeader* hdr, cudaStream_t s);
+// hdr->tau = min(hdr->tau, v) (v: the quantised energy of S known configurations or more)
+cudaError_t launch_tau_min(WsHeader* hdr, int v, cudaStream_t s);
 // Small instances (<= 2^kSmallFreeBits configurations): direct enumeration.
 // QUBO mapping (k_qubo.cu): dtype 0 = int32 in / int32 out (int64 offset), 1 = float in, 2 = double in
 // (double out and offset for both)

@@ -308,6 +308,15 @@ cudaError_t launch_seed(const Prep* prep, int n, int free_bits, unsigned long lo
     return cudaGetLastError();
 }
 
+__global__ void tau_min_kernel(WsHeader* hdr, int v) { atomicMin(&hdr->tau, v); }
+
+cudaError_t launch_tau_min(WsHeader* hdr, int v, cudaStream_t s)
+{
+    tau_min_kernel<<<1, 1, 0, s>>>(hdr, v);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_set_tau(const int* E, int S, WsHeader* hdr, cudaStream_t s)
 {
     set_tau_kernel<<<1, 1, 0, s>>>(E, S, hdr);
