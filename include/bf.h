@@ -337,8 +337,8 @@ bf_status bf_low_spectrum_qubo(const void* a, const void* b, int n, int S, bf_dt
  * for q = 2).  q^n <= 2^62.  Ties are broken by ascending c.  For q = 2 the
  * model is an Ising instance: with J' = J, h'_i = h_i(1) - h_i(0) and
  * C = sum_{i<j} J_ij + sum_i (h_i(0) + h_i(1)), 2 E(sigma) = E'(s) + C, and
- * q = 2 searches above 4096 configurations run as that Ising search (BF_EUNSUPPORTED
- * for integer h_i(1) - h_i(0) outside int32).
+ * q = 2 searches above 4096 configurations run as that Ising search (integer
+ * h_i(1) - h_i(0) outside int32: BF_EUNSUPPORTED from bf_workspace_status).
  *   J          device, n*n values of `dtype`, row-major; strict upper triangle read
  *   h          device, n*q values of `dtype`, row-major: h[i*q + v] = h_i(v)
  *   energies   device out, S values: int64 for BF_I32 (exact), double otherwise
@@ -346,8 +346,10 @@ bf_status bf_low_spectrum_qubo(const void* a, const void* b, int n, int S, bf_dt
  *   states     device out, S configuration integers
  *   workspace  device, >= bf_potts_workspace_size(...) bytes, 256-byte aligned
  * Options: task/grid/spill/profile fields as for bf_low_spectrum; fixed_bits
- * and the tensor-core variant are not supported (BF_EINVAL).  The call
- * synchronises once after its preparation kernel.
+ * and the tensor-core variant are not supported (BF_EINVAL).  The call does
+ * not synchronise (graph-capturable, with the same stream rule as
+ * bf_low_spectrum for its per-device tables); instances outside the int32
+ * fixed-point range are reported by bf_workspace_status (BF_EUNSUPPORTED).
  */
 size_t bf_potts_workspace_size(int n, int q, int S, bf_dtype dtype, const bf_options* opt);
 

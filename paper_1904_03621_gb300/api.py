@@ -164,7 +164,7 @@ def low_spectrum_qubo(a: torch.Tensor, b: torch.Tensor, S: int, *, variant: int 
 
 def low_spectrum_potts(J: torch.Tensor, h: torch.Tensor, S: int, *, task_log2: int = 0, grid_blocks: int = 0,
                        spill_log2: int = 0, profile: int = 0, stream=None, workspace: torch.Tensor | None = None,
-                       check: bool = True):
+                       check: bool = True, out: tuple | None = None):
     """S lowest (energy, configuration) pairs of the q-state Potts model.
 
     E(sigma) = sum_{i<j} J_ij [sigma_i == sigma_j] + sum_i h_i(sigma_i), sigma_i in {0..q-1};
@@ -190,8 +190,11 @@ def low_spectrum_potts(J: torch.Tensor, h: torch.Tensor, S: int, *, task_log2: i
     if workspace is None or workspace.numel() < nbytes:
         workspace = torch.empty(nbytes, dtype=torch.uint8, device=J.device)
     edt = torch.int64 if J.dtype == torch.int32 else torch.float64
-    energies = torch.empty(S, dtype=edt, device=J.device)
-    states = torch.empty(S, dtype=torch.int64, device=J.device)
+    if out is not None:
+        energies, states = out
+    else:
+        energies = torch.empty(S, dtype=edt, device=J.device)
+        states = torch.empty(S, dtype=torch.int64, device=J.device)
     sh = _stream_handle(stream)
     st = lib.bf_low_spectrum_potts(J.data_ptr(), h.data_ptr(), n, q, S, _DTYPES[J.dtype], energies.data_ptr(),
                                    states.data_ptr(), workspace.data_ptr(), workspace.numel(), ctypes.byref(o), sh)

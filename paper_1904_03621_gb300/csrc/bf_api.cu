@@ -31,40 +31,6 @@ struct ProfileEvents {
 };
 thread_local ProfileEvents g_prof;
 
-// Host copies of prep results that wait only for the work queued on the caller's stream
-// before side_mark(): the copy runs on a per-thread side stream behind an event, so the seed
-// kernels queued on the caller's stream in between keep the GPU busy while the host waits.
-struct SideStream {
-    cudaStream_t s = nullptr;
-    cudaEvent_t ev = nullptr;
-};
-constexpr int kMaxDevices = 64;
-thread_local SideStream g_side[kMaxDevices];
-
-cudaError_t side_mark(cudaStream_t stream, SideStream*& ss)
-{
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    ss = &g_side[dev];
-    if (!ss->s) {
-        e = cudaStreamCreateWithFlags(&ss->s, cudaStreamNonBlocking);
-        if (e != cudaSuccess) return e;
-        e = cudaEventCreateWithFlags(&ss->ev, cudaEventDisableTiming);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaEventRecord(ss->ev, stream);
-}
-
-cudaError_t side_copy(void* dst, const void* src, size_t bytes, SideStream* ss)
-{
-    cudaError_t e = cudaStreamWaitEvent(ss->s, ss->ev, 0);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, ss->s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ss->s);
-    return e;
-}
-
 bf_status fail(bf_status s, const char* fmt, ...)
 {
     char buf[512];
@@ -682,18 +648,14 @@ bf_status bf_low_spectrum_potts(const void* J, const void* h, int n, int q, int 
         cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(unsigned), stream);
         if (e == cudaSuccess) e = bf::launch_potts2_prep(J, h, n, (int)dtype, ws + pl.Jp, ws + pl.hp, ws + pl.cst, flag, stream);
         if (e != cudaSuccess) return cuda_fail(e, "two-state Potts map");
-        if (dtype == BF_I32) {
-            unsigned hflag = 0;
-            e = cudaMemcpyAsync(&hflag, flag, sizeof(hflag), cudaMemcpyDeviceToHost, stream);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-            if (e != cudaSuccess) return cuda_fail(e, "two-state Potts map status");
-            if (hflag) return fail(BF_EUNSUPPORTED, "h_i(1) - h_i(0) outside int32: use a float dtype");
-        }
+        // integer h_i(1) - h_i(0) outside int32 set the flag: preparation turns it into the
+        // out-of-range status (BF_EUNSUPPORTED from bf_workspace_status), nothing is walked
         const bf_dtype inner_dt = dtype == BF_I32 ? BF_I32 : BF_F64;
-        st = bf_low_spectrum(ws + pl.Jp, ws + pl.hp, n, S, inner_dt, energies, states, workspace, pl.inner, opt,
-                             stream_ptr);
+        st = low_spectrum_impl(ws + pl.Jp, ws + pl.hp, n, S, inner_dt, energies, states, workspace, pl.inner, opt,
+                               stream_ptr, dtype == BF_I32 ? flag : nullptr);
         if (st != BF_OK) return st;
-        e = bf::launch_potts2_finish(energies, S, dtype == BF_I32 ? 0 : 1, ws + pl.cst, &hdr->status, stream);
+        e = bf::launch_potts2_finish(energies, S, dtype == BF_I32 ? 0 : 1, ws + pl.cst, &hdr->status, stream,
+                                     dtype == BF_I32 ? flag : nullptr);
         if (e != cudaSuccess) return cuda_fail(e, "two-state Potts energies");
         return BF_OK;
     }
@@ -701,13 +663,10 @@ bf_status bf_low_spectrum_potts(const void* J, const void* h, int n, int q, int 
     auto* prep = reinterpret_cast<bf::PottsPrep*>(ws + pl.prep_off);
     cudaError_t e = bf::launch_potts_prep(J, h, n, q, (int)dtype, prep, hdr, stream);
     if (e != cudaSuccess) return cuda_fail(e, "Potts prep kernel");
-    // per-instance constants become kernel parameters of the walk
-    struct { int q, status, qs, W; double delta, emax; int dT[bf::kPottsMaxSteps]; unsigned dT16[bf::kPottsMaxSteps]; } hp;
-    static_assert(offsetof(bf::PottsPrep, dT) == 32, "PottsPrep header layout");
-    static_assert(offsetof(bf::PottsPrep, dT16) == 32 + 4 * bf::kPottsMaxSteps, "PottsPrep header layout");
-    SideStream* side = nullptr;
-    e = side_mark(stream, side);
-    if (e != cudaSuccess) return cuda_fail(e, "Potts prep event");
+    // the walk's constants stay on the device (constant tables filled by launch_potts_walk, the
+    // window and scale read from prep by the kernels): no host synchronisation
+    const int* Wd = &prep->W;
+    const int* qsd = &prep->qs;
 
     int* AE = reinterpret_cast<int*>(ws + L.listA_E);
     auto* AC = reinterpret_cast<unsigned long long*>(ws + L.listA_C);
@@ -722,14 +681,7 @@ bf_status bf_low_spectrum_potts(const void* J, const void* h, int n, int q, int 
     e = bf::launch_set_tau(in_a ? AE : BE, S, hdr, stream);
     if (e != cudaSuccess) return cuda_fail(e, "Potts seed threshold");
 
-    // the seed runs while the host waits for the per-instance walk constants
-    e = side_copy(&hp, prep, sizeof(hp), side);
-    if (e != cudaSuccess) return cuda_fail(e, "Potts prep copy");
-    if (hp.status & bf::kErrRange) return fail(BF_EUNSUPPORTED, "instance outside the fixed-point range");
-
     bf::PottsParams pp{};
-    std::memcpy(pp.dT, hp.dT, sizeof(pp.dT));
-    std::memcpy(pp.dT16, hp.dT16, sizeof(pp.dT16));
     for (int i = 0; i <= bf::kMaxN; i++) pp.qpow[i] = i <= n ? bf::potts_pow(q, i) : 0ull;
     pp.n = n;
     pp.q = q;
@@ -738,7 +690,6 @@ bf_status bf_low_spectrum_potts(const void* J, const void* h, int n, int q, int 
     pp.ntasks = pl.ntasks;
     pp.S = S;
     pp.list_cap = L.list_cap;
-    pp.W = hp.W;
     pp.seg_log2 = pl.seg_log2;
     pp.spill_cap = L.spill_cap;
     pp.prep = prep;
@@ -765,11 +716,12 @@ bf_status bf_low_spectrum_potts(const void* J, const void* h, int n, int q, int 
         if (e != cudaSuccess) return cuda_fail(e, "profile event");
         g_prof.valid = true;
     }
-    e = bf::launch_absorb_spill(AE, AC, pl.grid, L.list_cap, S, hp.W, pp.spill_E, pp.spill_C, L.spill_cap, hdr, stream);
+    e = bf::launch_absorb_spill(AE, AC, pl.grid, L.list_cap, S, 0, pp.spill_E, pp.spill_C, L.spill_cap, hdr, stream,
+                                Wd);
     if (e != cudaSuccess) return cuda_fail(e, "spill absorb");
-    e = merge_tree(AE, AC, BE, BC, pl.grid, L.list_cap, S, hp.W, hdr, stream, in_a);
+    e = merge_tree(AE, AC, BE, BC, pl.grid, L.list_cap, S, 0, hdr, stream, in_a, Wd);
     if (e != cudaSuccess) return cuda_fail(e, "merge rounds");
-    e = bf::launch_potts_finalize(in_a ? AE : BE, in_a ? AC : BC, L.list_cap, S, n, q, (int)dtype, hp.qs, J, h,
+    e = bf::launch_potts_finalize(in_a ? AE : BE, in_a ? AC : BC, L.list_cap, S, n, q, (int)dtype, qsd, J, h,
                                   reinterpret_cast<double*>(ws + L.rescore), energies, out_states, stream);
     if (e != cudaSuccess) return cuda_fail(e, "Potts finalize");
     return BF_OK;

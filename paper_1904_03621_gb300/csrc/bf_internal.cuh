@@ -245,13 +245,13 @@ struct PottsPrep {                       // written by potts_prep_kernel (device
     int hq[kMaxN * kPottsMaxQ];          // quantised fields h_i(v), row stride q
 };
 
+// The walk reads PottsPrep::dT and ::dT16 from __constant__ tables that launch_potts_walk fills
+// from the workspace (device-to-device, stream-ordered) and the window W from the workspace.
 struct PottsParams {
-    int dT[kPottsMaxSteps];              // copy of PottsPrep::dT (kernel-parameter constants)
-    unsigned dT16[kPottsMaxSteps];       // copy of PottsPrep::dT16
     unsigned long long qpow[kMaxN + 1];  // q^i
     int n, q, B, m;                      // spins, states, inner digits, walked middle digits
     unsigned long long ntasks;           // q^(n - B - m)
-    int S, list_cap, W, seg_log2;
+    int S, list_cap, seg_log2;
     unsigned spill_cap;
     int pad0;
     const PottsPrep* prep;
@@ -271,8 +271,9 @@ cudaError_t launch_potts_walk(const PottsParams& p, int grid, cudaStream_t s);
 int potts_walk_blocks_per_sm(int q, int m, int n, int list_cap);
 cudaError_t launch_potts_direct(const void* J, const void* h, int n, int q, int dtype, int S, void* energies,
                                 unsigned long long* states, WsHeader* hdr, cudaStream_t s);
+// qsp: device, the fixed-point scale exponent (PottsPrep::qs)
 cudaError_t launch_potts_finalize(const int* E, const unsigned long long* C, int cap, int S, int n, int q,
-                                  int dtype, int qs, const void* J, const void* h, double* rescore,
+                                  int dtype, const int* qsp, const void* J, const void* h, double* rescore,
                                   void* energies, unsigned long long* states, cudaStream_t s);
 
 // ---- batched search ----------------------------------------------------
@@ -401,7 +402,9 @@ cudaError_t launch_qubo_finish(void* F, int S, int dtype, const void* off4, unsi
 // C = sum_{i<j} J_ij + sum_i (h_i(0) + h_i(1)); energies E = (E' + C) / 2 (same dtypes as the QUBO map)
 cudaError_t launch_potts2_prep(const void* J, const void* h, int n, int dtype, void* Jout, void* hout, void* cst,
                                unsigned* flag, cudaStream_t s);
-cudaError_t launch_potts2_finish(void* E, int S, int dtype, const void* cst, unsigned* flag, cudaStream_t s);
+// map_flag (optional, integer form): nonzero marks the search out of range in *flag (the status word)
+cudaError_t launch_potts2_finish(void* E, int S, int dtype, const void* cst, unsigned* flag, cudaStream_t s,
+                                 const unsigned* map_flag = nullptr);
 cudaError_t launch_direct(const void* J, const void* h, int n, int dtype, int S, int free_bits,
                           unsigned long long hiconst, void* energies, unsigned long long* states,
                           WsHeader* hdr, cudaStream_t s);

@@ -30,6 +30,8 @@
 // instances).  Selection, segments and the spill area follow gray_kernel.
 #include <cfloat>
 #include <climits>
+#include <cstddef>
+#include <mutex>
 #include <type_traits>
 #include <utility>
 
@@ -38,6 +40,11 @@
 
 namespace bf {
 namespace {
+
+// inner pair-table differences of the search being run (PottsPrep::dT, exact, and ::dT16, the
+// 16-bit views in both lanes), copied in by launch_potts_walk; constant-bank operands of the walk
+__constant__ int c_pdT[kPottsMaxSteps];
+__constant__ unsigned c_pdT16[kPottsMaxSteps];
 
 constexpr int kPottsThreads = 256;
 constexpr int kPottsPrepThreads = 256;
@@ -264,7 +271,7 @@ __device__ __forceinline__ void potts_step(unsigned& X, unsigned& X1, unsigned& 
     constexpr int a0 = potts_gray_digit(t - 1, Q, k), a1 = potts_gray_digit(t, Q, k);
     constexpr bool up = a1 > a0;
     constexpr int v = up ? a0 : a1;
-    X += (up ? G[k][v] : 0u - G[k][v]) + p.dT16[t];
+    X += (up ? G[k][v] : 0u - G[k][v]) + c_pdT16[t];
     if constexpr ((t & 1) != 0) {
         X1 = X;
     } else {
@@ -350,7 +357,7 @@ __device__ __forceinline__ void potts_warp_rescan(const PottsParams& p, const Po
         if (t > t0) {
             const int st = s.step[t];
             const unsigned g = (unsigned)G[(st >> 1) * kPottsThreads];
-            e += ((st & 1) ? g : 0u - g) + (unsigned)p.dT[t];
+            e += ((st & 1) ? g : 0u - g) + (unsigned)c_pdT[t];
         }
         const int ei = (int)e;
         const unsigned long long c = cb + (unsigned long long)s.xin[t];
@@ -391,6 +398,14 @@ __global__ void __launch_bounds__(kPottsThreads, 2) potts_walk_kernel(const __gr
 
     const int tid = threadIdx.x;
     const PottsPrep* prep = p.prep;
+    if (*(volatile unsigned*)&p.hdr->status & kErrRange) {
+        // the instance is outside the fixed-point range (reported by the workspace status): no walk
+        for (int i = tid; i < cap; i += blockDim.x) {
+            p.list_E[(size_t)blockIdx.x * cap + i] = kEmptyE;
+            p.list_C[(size_t)blockIdx.x * cap + i] = kEmptyC;
+        }
+        return;
+    }
     for (int i = tid; i < n * n; i += blockDim.x) s.Jq[i] = prep->Jq[i];
     for (int i = tid; i < n * Q; i += blockDim.x) s.hq[i] = prep->hq[i];
     for (int t = tid; t < P; t += blockDim.x) {
@@ -414,7 +429,7 @@ __global__ void __launch_bounds__(kPottsThreads, 2) potts_walk_kernel(const __gr
     }
     __syncthreads();
 
-    const int S = p.S, W = p.W;
+    const int S = p.S, W = prep->W;
     const unsigned long long nblocks = p.qpow[m];
     const unsigned long long seg_mask = (1ull << p.seg_log2) - 1ull;
     const unsigned long long task_mul = p.qpow[B + m];
@@ -724,9 +739,10 @@ __global__ void __launch_bounds__(kPottsDirectThreads) potts_direct_kernel(const
     }
 }
 
-__global__ void potts_finalize_int_kernel(const int* E, const unsigned long long* C, int S, int qs, long long* out,
-                                          unsigned long long* states)
+__global__ void potts_finalize_int_kernel(const int* E, const unsigned long long* C, int S, const int* qsp,
+                                          long long* out, unsigned long long* states)
 {
+    const int qs = *qsp;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < S; k += gridDim.x * blockDim.x) {
         out[k] = (long long)(E[k] >> qs);
         states[k] = C[k];
@@ -785,12 +801,46 @@ int potts_walk_blocks_per_sm(int q, int m, int n, int list_cap)
     return bps;
 }
 
+namespace {
+
+// The tables are one per device: a launch waits for the previous Potts walk on the device (an
+// event recorded after it) before overwriting them, except inside a stream capture, where that
+// event cannot be waited on (a captured search relies on the order of the graph's launches).
+constexpr int kPottsMaxDevices = 64;
+std::mutex g_ptable_mutex;
+cudaEvent_t g_ptable_free[kPottsMaxDevices];
+
+}  // namespace
+
 cudaError_t launch_potts_walk(const PottsParams& p, int grid, cudaStream_t s)
 {
     if (p.q < 3 || p.q > kPottsMaxQ) return cudaErrorInvalidValue;
     const size_t smem = potts_walk_smem(p.q, p.n, p.list_cap);
     const void* fn = walk_for(p.q);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kPottsMaxDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
+    const bool ordered = cs == cudaStreamCaptureStatusNone;
+    std::lock_guard<std::mutex> lock(g_ptable_mutex);
+    if (ordered) {
+        if (!g_ptable_free[dev]) {
+            e = cudaEventCreateWithFlags(&g_ptable_free[dev], cudaEventDisableTiming);
+            if (e != cudaSuccess) return e;
+        }
+        e = cudaStreamWaitEvent(s, g_ptable_free[dev], 0);
+        if (e != cudaSuccess) return e;
+    }
+    const char* prep = reinterpret_cast<const char*>(p.prep);
+    e = cudaMemcpyToSymbolAsync(c_pdT, prep + offsetof(PottsPrep, dT), sizeof(c_pdT), 0, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyToSymbolAsync(c_pdT16, prep + offsetof(PottsPrep, dT16), sizeof(c_pdT16), 0,
+                                    cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return e;
     switch (p.q) {
     case 3: potts_walk_kernel<3><<<grid, kPottsThreads, smem, s>>>(p); break;
@@ -801,7 +851,9 @@ cudaError_t launch_potts_walk(const PottsParams& p, int grid, cudaStream_t s)
     default: potts_walk_kernel<8><<<grid, kPottsThreads, smem, s>>>(p); break;
     }
     count_launches(1);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return ordered ? cudaEventRecord(g_ptable_free[dev], s) : cudaSuccess;
 }
 
 cudaError_t launch_potts_direct(const void* J, const void* h, int n, int q, int dtype, int S, void* energies,
@@ -829,11 +881,11 @@ cudaError_t launch_potts_direct(const void* J, const void* h, int n, int q, int 
 }
 
 cudaError_t launch_potts_finalize(const int* E, const unsigned long long* C, int cap, int S, int n, int q, int dtype,
-                                  int qs, const void* J, const void* h, double* rescore, void* energies,
+                                  const int* qsp, const void* J, const void* h, double* rescore, void* energies,
                                   unsigned long long* states, cudaStream_t s)
 {
     if (dtype == 0) {
-        potts_finalize_int_kernel<<<(S + 255) / 256, 256, 0, s>>>(E, C, S, qs, static_cast<long long*>(energies),
+        potts_finalize_int_kernel<<<(S + 255) / 256, 256, 0, s>>>(E, C, S, qsp, static_cast<long long*>(energies),
                                                                   states);
         count_launches(1);
         return cudaGetLastError();

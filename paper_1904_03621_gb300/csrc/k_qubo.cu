@@ -94,9 +94,11 @@ __global__ void __launch_bounds__(kQThreads) potts2_prep_kernel(const T* J, cons
 }
 
 // E[k] = (E'[k] + C) / 2
-__global__ void potts2_finish_i64_kernel(long long* E, int S, const long long* cst, unsigned* flag)
+__global__ void potts2_finish_i64_kernel(long long* E, int S, const long long* cst, unsigned* flag,
+                                         const unsigned* map_flag)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0 && map_flag && *map_flag) atomicOr(flag, kErrRange);   // h' left int32: the search was void
     if (k >= S) return;
     const long long v = E[k] + *cst;
     if (v & 1ll) atomicOr(flag, 2u);       // cannot happen for a consistent instance
@@ -169,12 +171,13 @@ cudaError_t launch_potts2_prep(const void* J, const void* h, int n, int dtype, v
     return cudaGetLastError();
 }
 
-cudaError_t launch_potts2_finish(void* E, int S, int dtype, const void* cst, unsigned* flag, cudaStream_t s)
+cudaError_t launch_potts2_finish(void* E, int S, int dtype, const void* cst, unsigned* flag, cudaStream_t s,
+                                 const unsigned* map_flag)
 {
     const int blocks = (S + 255) / 256;
     if (dtype == 0)
         potts2_finish_i64_kernel<<<blocks, 256, 0, s>>>(static_cast<long long*>(E), S,
-                                                        static_cast<const long long*>(cst), flag);
+                                                        static_cast<const long long*>(cst), flag, map_flag);
     else
         potts2_finish_f64_kernel<<<blocks, 256, 0, s>>>(static_cast<double*>(E), S, static_cast<const double*>(cst));
     count_launches(1);

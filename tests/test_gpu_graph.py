@@ -92,3 +92,43 @@ def test_two_streams_at_once(bf):
     torch.cuda.synchronize()
     for (J, h), (en, st, _, _) in zip(cases, outs):
         compare(o, J, h, en, st, 200)
+
+
+@pytest.mark.parametrize("q,n,S", [(3, 10, 50), (4, 8, 30), (2, 16, 40)])
+def test_potts_graph_capture_and_replay(bf, q, n, S):
+    """The q-state Potts search (walk for q >= 3, the Ising map for q = 2) captured and replayed
+    with new values written into the captured inputs."""
+    import torch
+    from paper_1904_03621_gb300 import _lib
+    o = oracle.get()
+    rng = np.random.default_rng(40 + q)
+
+    def draw():
+        J = np.triu(rng.standard_normal((n, n)), 1)
+        return J + J.T, rng.standard_normal((n, q))
+    J, h = draw()
+    Jd = torch.from_numpy(np.ascontiguousarray(J)).cuda()
+    hd = torch.from_numpy(np.ascontiguousarray(h)).cuda()
+    lib = _lib.load()
+    import ctypes
+    o_ = bf._options()
+    ws = torch.empty(int(lib.bf_potts_workspace_size(n, q, S, _lib.BF_F64, ctypes.byref(o_))), dtype=torch.uint8,
+                     device="cuda")
+    en = torch.empty(S, dtype=torch.float64, device="cuda")
+    st = torch.empty(S, dtype=torch.int64, device="cuda")
+    bf.low_spectrum_potts(Jd, hd, S, workspace=ws, out=(en, st))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        bf.low_spectrum_potts(Jd, hd, S, workspace=ws, out=(en, st), check=False)
+    for rep in range(2):
+        if rep == 1:
+            J, h = draw()
+            Jd.copy_(torch.from_numpy(np.ascontiguousarray(J)))
+            hd.copy_(torch.from_numpy(np.ascontiguousarray(h)))
+        en.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        _lib.check(lib.bf_workspace_status(ws.data_ptr(), None), lib)
+        e_o, s_o = o.potts_low_spectrum(J, h, S)
+        assert np.abs(en.cpu().numpy() - e_o).max() <= 1e-9 * (np.abs(np.triu(J, 1)).sum() + np.abs(h).sum())
+        assert np.array_equal(bf.states_u64(st), s_o)
