@@ -526,21 +526,35 @@ __device__ int warp_merge(int* E, unsigned long long* C, int count, int S, int W
     return keep;
 }
 
+// The running minimum is kept per eighth of the block (kBPart steps each): a flagged walk is
+// rescanned only in the parts whose minimum reached the threshold.
+constexpr int kBParts = 8;
+constexpr int kBPart = kBWalkSteps / kBParts;
+static_assert(kBPart % 32 == 0 && 2 * kBParts <= 32, "a part is whole Gray steps per lane; flags fit one word");
+
+struct BPacked {
+    unsigned Xa, Xb;
+    unsigned M[kBParts];
+    unsigned Ga[kBWalkBits], Gb[kBWalkBits];
+};
+
 template <int t>
-__device__ __forceinline__ void bstep(Packed<kBWalkBits>& w, unsigned d)
+__device__ __forceinline__ void bstep(BPacked& w, unsigned d)
 {
     if constexpr (t > 0) {
         constexpr int k = cx_ctz(t);
         constexpr bool up = cx_up(t);
+        constexpr int part = t / kBPart;
         w.Xa += (up ? w.Ga[k] : 0u - w.Ga[k]) + d;
         w.Xb += (up ? w.Gb[k] : 0u - w.Gb[k]) + d;
-        w.M = __vminu2(__vminu2(w.M, w.Xa), w.Xb);
+        if constexpr (t % kBPart == 0) w.M[part] = __vminu2(w.Xa, w.Xb);
+        else w.M[part] = __vminu2(__vminu2(w.M[part], w.Xa), w.Xb);
     }
 }
 
 // four steps per 128-bit shared-memory load of the instance's increments
 template <int g>
-__device__ __forceinline__ void bwalk_group(Packed<kBWalkBits>& w, const uint4* tab4)
+__device__ __forceinline__ void bwalk_group(BPacked& w, const uint4* tab4)
 {
     const uint4 d = tab4[g];
     bstep<4 * g + 0>(w, d.x);
@@ -550,7 +564,7 @@ __device__ __forceinline__ void bwalk_group(Packed<kBWalkBits>& w, const uint4* 
 }
 
 template <int... Gs>
-__device__ __forceinline__ void bwalk_block(Packed<kBWalkBits>& w, const uint4* tab4, std::integer_sequence<int, Gs...>)
+__device__ __forceinline__ void bwalk_block(BPacked& w, const uint4* tab4, std::integer_sequence<int, Gs...>)
 {
     (bwalk_group<Gs>(w, tab4), ...);
 }
@@ -671,7 +685,7 @@ __global__ void __launch_bounds__(kBThreads, 2) bwalk_kernel(const BatchParams p
                 }
             }
         }
-        Packed<kBWalkBits> pk;
+        BPacked pk;
 #pragma unroll
         for (int k = 0; k < kBWalkBits; k++) {
             pk.Ga[k] = pack_hi16(G[0][k], G[1][k]);
@@ -705,9 +719,15 @@ __global__ void __launch_bounds__(kBThreads, 2) bwalk_kernel(const BatchParams p
             if (reread) tg_early = *(volatile int*)&p.tau[b];
             pk.Xa = pack_energy(E0[0], E0[1]);
             pk.Xb = pack_energy(E0[2], E0[3]);
-            pk.M = __vminu2(pk.Xa, pk.Xb);
+            pk.M[0] = __vminu2(pk.Xa, pk.Xb);
             bwalk_block(pk, reinterpret_cast<const uint4*>(dTw), std::make_integer_sequence<int, kBWalkSteps / 4>{});
-            const unsigned flags = (((pk.M & 0xffffu) <= thr16) ? 1u : 0u) | (((pk.M >> 16) <= thr16) ? 2u : 0u);
+            // bit 2 part + lane: the 16-bit lane (walks 0 and 2 share lane 0, walks 1 and 3 lane 1)
+            // whose minimum over that part of the block reached the threshold
+            unsigned flags = 0u;
+#pragma unroll
+            for (int part = 0; part < kBParts; part++)
+                flags |= ((((pk.M[part] & 0xffffu) <= thr16) ? 1u : 0u) | (((pk.M[part] >> 16) <= thr16) ? 2u : 0u))
+                         << (2 * part);
             const unsigned bal = __ballot_sync(0xffffffffu, flags != 0u);
             if (bal) {
                 // warp-cooperative exact rescan of every flagged walk
@@ -717,7 +737,9 @@ __global__ void __launch_bounds__(kBThreads, 2) bwalk_kernel(const BatchParams p
                     const unsigned aL = __shfl_sync(0xffffffffu, active_mask, L);
 #pragma unroll
                     for (int w = 0; w < kWalks; w++) {
-                        if (!((fL >> (w & 1)) & 1u) || !((aL >> w) & 1u)) continue;
+                        // this walk's lane in every part (bits 2 part)
+                        const unsigned parts = (fL >> (w & 1)) & (0x55555555u >> (32 - 2 * kBParts));
+                        if (!parts || !((aL >> w) & 1u)) continue;
                         const int e0 = __shfl_sync(0xffffffffu, E0[w], L);
                         if (lane == L) {
 #pragma unroll
@@ -725,17 +747,19 @@ __global__ void __launch_bounds__(kBThreads, 2) bwalk_kernel(const BatchParams p
                         }
                         const unsigned long long cb = __shfl_sync(0xffffffffu, cfg0[w], L) | cmid;
                         __syncwarp();
-                        // lane l walks Gray steps t = l R .. l R + R - 1 of the block: it sums the fields of
-                        // its first configuration, then follows one flip per step
-                        constexpr unsigned R = kBWalkSteps / 32;
+                        // in each flagged part, lane l walks the Gray steps t = P + l R .. P + l R + R - 1:
+                        // it sums the fields of its first configuration, then follows one flip per step
+                        constexpr unsigned R = kBPart / 32;
                         const int* Gs = s_g[wid];
                         const unsigned base_e = (unsigned)e0 - (unsigned)Tw[0];
-                        unsigned t = (unsigned)lane * R;
+                        for (unsigned prest = parts; prest; prest &= prest - 1u) {
+                        const unsigned part = (unsigned)(__ffs(prest) - 1) >> 1;
+                        unsigned t = part * kBPart + (unsigned)lane * R;
                         unsigned g = t ^ (t >> 1);
                         unsigned sg = 0u;
 #pragma unroll
                         for (int k = 0; k < kBWalkBits; k++) sg += ((g >> k) & 1u) ? (unsigned)Gs[k] : 0u;
-#pragma unroll 4
+#pragma unroll
                         for (unsigned i = 0; i < R; i++) {
                             if (count > kBBuf - 32) {
                                 // room for the next 32 records: merge first (count is warp-uniform)
@@ -759,6 +783,7 @@ __global__ void __launch_bounds__(kBThreads, 2) bwalk_kernel(const BatchParams p
                                 Cw[slot] = c;
                             }
                             count += __popc(hb);
+                        }
                         }
                         __syncwarp();
                     }
