@@ -427,31 +427,6 @@ bf_status low_spectrum_impl(const void* J, const void* h, int n, int S, bf_dtype
         g_prof.valid = true;
     }
 
-    if (pl.grid <= bf::kMaxGatherLists) {
-        // one launch: the list prefixes and spill records below tau + W, selection, finalisation
-        bf::GatherParams gq{};
-        gq.list_E = AE;
-        gq.list_C = AC;
-        gq.nlists = pl.grid;
-        gq.cap = L.list_cap;
-        gq.spill_E = gp.spill_E;
-        gq.spill_C = gp.spill_C;
-        gq.spill_cap = L.spill_cap;
-        gq.S = S;
-        gq.buf = bf::gather_buffer(L.list_cap);
-        gq.Wp = Wd;
-        gq.qp = qd;
-        gq.n = n;
-        gq.dtype = dtype;
-        gq.J = J;
-        gq.h = h;
-        gq.energies = energies;
-        gq.states = out_states;
-        gq.hdr = hdr;
-        e = bf::launch_gather_final(gq, stream);
-        if (e != cudaSuccess) return cuda_fail(e, "final selection");
-        return BF_OK;
-    }
     e = bf::launch_absorb_spill(AE, AC, pl.grid, L.list_cap, S, 0, gp.spill_E, gp.spill_C, L.spill_cap, hdr, stream,
                                 Wd);
     if (e != cudaSuccess) return cuda_fail(e, "spill absorb");

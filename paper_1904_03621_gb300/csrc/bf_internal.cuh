@@ -343,31 +343,6 @@ cudaError_t launch_merge_round(const int* inE, const unsigned long long* inC, in
 cudaError_t launch_absorb_spill(int* E, unsigned long long* C, int nlists, int cap, int S, int W,
                                 const int* spill_E, const unsigned long long* spill_C,
                                 unsigned spill_cap, WsHeader* hdr, cudaStream_t s, const int* Wp = nullptr);
-// Final selection of one search in a single launch (k_gather.cu): the prefixes of the sorted
-// block lists and the spill records with E <= tau + W are gathered, kept by the selection rule
-// and finalised (E_q >> q for integer instances, FP64 re-evaluation and reselection otherwise).
-constexpr int kMaxGatherLists = 1024;
-struct GatherParams {
-    const int* list_E;
-    const unsigned long long* list_C;
-    int nlists, cap;                // sorted lists of cap records each
-    const int* spill_E;
-    const unsigned long long* spill_C;
-    unsigned spill_cap;
-    int S, buf;                     // buf: shared-memory records (power of two, >= 2 cap)
-    const int* Wp;                  // device: candidate window
-    const int* qp;                  // device: fixed-point scale exponent
-    int n, dtype;
-    const void* J;
-    const void* h;
-    void* energies;
-    unsigned long long* states;
-    WsHeader* hdr;
-};
-size_t gather_smem_bytes(int nlists, int cap, int buf, int n);
-int gather_buffer(int cap);
-cudaError_t launch_gather_final(const GatherParams& p, cudaStream_t s);
-
 // Final selection: integer instances write E_q >> q; float instances
 // re-evaluate Eq. (1) in FP64 from the caller's J, h and reselect.
 // qp != nullptr: the scale exponent is read on the device from *qp instead of q.
