@@ -96,7 +96,9 @@ typedef enum {
  *                usable.  Ignored by the other kernels.
  *   inner_bits   spins walked by the fully unrolled block of the Gray-code walk:
  *                0 = automatic (10 for searches of at least 2^42 configurations
- *                and 9 below), or 9 or 10 (10 needs n >= 14).  Results do not
+ *                and 9 below; spaces of at most 2^20 configurations are then
+ *                enumerated exactly by the seed kernel, without a walk), or 9 or
+ *                10 (10 needs n >= 14), which always walks.  Results do not
  *                depend on it.  Ignored by the tensor-core variant.
  * When variant, inner_bits, task_log2 and grid_blocks are all 0 and bf_autotune
  * has run for this device and (n, n - fixed_bits, S, dtype), its choice is used.
@@ -156,11 +158,13 @@ bf_status bf_low_spectrum(const void* J, const void* h, int n, int S, bf_dtype d
  * bf_autotune -- choose the screening kernel and launch shape of bf_low_spectrum
  * for one search size by timing candidates on this GPU (CUDA events on
  * `stream`), as the paper chooses its launch configuration by measurement
- * (Sec. 4.2).  Candidates: the Gray-code walk with 9 and 10 inner spins, the
- * default task length (task_log2) and lengths 2^2 and 2^4 shorter and 2^2
- * longer (at most 2^14 blocks per task), 1 or 2 blocks per SM; the
- * tensor-core variant with three task lengths where n - fixed_bits >= 15.  Each candidate runs bf_low_spectrum's
- * plan on J, h (arguments as for bf_low_spectrum; `base` supplies fixed_bits,
+ * (Sec. 4.2).  Candidates: for spaces of at most 2^20 configurations the
+ * exact enumeration by the seed kernel alone (the default there); the
+ * Gray-code walk with 9 and 10 inner spins, the default task length
+ * (task_log2) and lengths 2^2 and 2^4 shorter and 2^2 longer (at most 2^14
+ * blocks per task), 1 or 2 blocks per SM; the tensor-core variant with three
+ * task lengths where n - fixed_bits >= 15.  Each candidate runs
+ * bf_low_spectrum's plan on J, h (arguments as for bf_low_spectrum; `base` supplies fixed_bits,
  * fixed_value and spill_log2, may be NULL).  Searches of more than 2^39
  * configurations time only the end of the task queue: at least 2^39
  * configurations and two batches of tasks per block (same task shape as the

@@ -81,6 +81,7 @@ struct Plan {
     int variant;
     int list_cap, grid, m, nh, seg_log2, seed_per_block, seed_blocks, inner_bits;
     int descent_blocks;             // > 0: local-search seed instead of the sampled one
+    bool sample_only;               // the seed enumerates the whole space: its lists are the answer
     unsigned long long seed_sample;
     bf::Layout L;
     size_t bytes;
@@ -175,7 +176,11 @@ bf_status make_plan(int n, int S, int dtype, const bf_options* opt, Plan& pl)
     // searches start from the same threshold quality
     pl.seed_per_block = std::max(pl.list_cap, 2048);
     unsigned long long sample = 1ull << std::min(free_bits, bf::kSeedLog2);
-    sample = std::min(sample, (unsigned long long)full_grid * pl.seed_per_block);
+    // spaces of at most 2^20 configurations: the seed evaluates every configuration (exact
+    // energies, one sorted list per seed block) and its merged lists are the answer, so the walk
+    // and its selection are skipped (Gray walk searches with the automatic block size only)
+    pl.sample_only = free_bits <= bf::kSeedLog2 && pl.variant == BF_VARIANT_GRAY && o.inner_bits == 0;
+    if (!pl.sample_only) sample = std::min(sample, (unsigned long long)full_grid * pl.seed_per_block);
     pl.seed_sample = sample;
     pl.seed_blocks = (int)((sample + pl.seed_per_block - 1) / pl.seed_per_block);
     // beyond 2^kSeedLog2 configurations the sample no longer covers the space: a local search
@@ -319,6 +324,24 @@ bf_status low_spectrum_impl(const void* J, const void* h, int n, int S, bf_dtype
     auto* BC = reinterpret_cast<unsigned long long*>(ws + L.listB_C);
     bool in_a = true;
 
+    const int* Wd = &prep->L.W;
+    const int* qd = &prep->L.q;
+    if (pl.sample_only) {
+        // every configuration evaluated exactly by the seed kernel; the merges keep the S lowest
+        // plus the float window, and a seed block whose dropped records could reach the window
+        // flags BF_EOVERFLOW
+        e = bf::launch_seed(prep, n, pl.free_bits, pl.hiconst, pl.seed_sample, pl.seed_per_block, pl.seed_blocks,
+                            L.list_cap, AE, AC, stream, S, hdr);
+        if (e != cudaSuccess) return cuda_fail(e, "seed kernel");
+        e = merge_tree(AE, AC, BE, BC, pl.seed_blocks, L.list_cap, S, 0, hdr, stream, in_a, Wd);
+        if (e != cudaSuccess) return cuda_fail(e, "seed merge");
+        e = bf::launch_finalize(in_a ? AE : BE, in_a ? AC : BC, L.list_cap, S, n, dtype, 0, J, h,
+                                reinterpret_cast<double*>(ws + L.rescore), energies, out_states, hdr, stream, qd);
+        if (e != cudaSuccess) return cuda_fail(e, "finalize");
+        if (walked) *walked = (double)(1ull << pl.free_bits);
+        return BF_OK;
+    }
+
     // seed threshold: the S-th lowest quantised energy of a pseudo-random sample, and / or of the
     // Hamming balls around local-search minima (alone when the first ball holds S configurations)
     const bool ball_only = pl.descent_blocks && bf::ball_size(pl.free_bits) >= S;
@@ -343,8 +366,6 @@ bf_status low_spectrum_impl(const void* J, const void* h, int n, int S, bf_dtype
     // from the workspace by the kernels, and an instance outside the fixed-point range sets a
     // status bit that stops the walk and is reported by bf_workspace_status.  No host
     // synchronisation: the call can be captured in a CUDA graph.
-    const int* Wd = &prep->L.W;
-    const int* qd = &prep->L.q;
 
     bf::GrayParams gp{};
     gp.n = n;
@@ -968,6 +989,11 @@ extern "C" bf_status bf_autotune(const void* J, const void* h, int n, int S, bf_
     // candidates: the Gray walk with 9 and 10 inner spins, the default task length and two
     // either side of it, 1 or 2 blocks per SM; the tensor-core variant where it applies
     std::vector<bf_options> cand;
+    if (!pl0.direct && pl0.free_bits <= bf::kSeedLog2) {
+        bf_options c = b0;                           // the exact sample of the whole space, no walk
+        c.variant = BF_VARIANT_GRAY;
+        cand.push_back(c);
+    }
     if (!pl0.direct) {
         const int bps = bf::gray_blocks_per_sm(bf::list_capacity(S));
         for (int ib : {9, 10}) {

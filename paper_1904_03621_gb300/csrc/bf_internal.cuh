@@ -351,9 +351,11 @@ cudaError_t launch_finalize(const int* E, const unsigned long long* C, int cap, 
                             void* energies, unsigned long long* states, WsHeader* hdr, cudaStream_t s,
                             const int* qp = nullptr);
 // Seed: `blocks` lists of the lowest sampled records (sample configurations in total).
+// With hdr != nullptr (a sample of the whole space whose lists are the answer), a block whose
+// first dropped record lies within its S-th energy + W flags kErrWindow.
 cudaError_t launch_seed(const Prep* prep, int n, int free_bits, unsigned long long hiconst,
                         unsigned long long sample, int per_block, int blocks, int cap, int* outE,
-                        unsigned long long* outC, cudaStream_t s);
+                        unsigned long long* outC, cudaStream_t s, int S = 0, WsHeader* hdr = nullptr);
 // Local-search seed (k_descent.cu): `blocks` descent blocks, then the S-th lowest distinct
 // energy of the radius-2 Hamming balls around the lowest minima found becomes hdr->tau
 // (assign; needs ball_size(free_bits) >= S) or lowers it (atomicMin).

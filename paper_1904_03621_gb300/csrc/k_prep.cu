@@ -196,7 +196,8 @@ constexpr unsigned long long kSeedMul = 0x9E3779B97F4A7C15ull;
 __global__ void __launch_bounds__(kSeedThreads) seed_kernel(const Prep* prep, int n, int free_bits,
                                                              unsigned long long hiconst,
                                                              unsigned long long sample, int per_block, int cap,
-                                                             int* outE, unsigned long long* outC)
+                                                             int* outE, unsigned long long* outC, int S,
+                                                             WsHeader* hdr)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long* C = reinterpret_cast<unsigned long long*>(smem);   // per_block
@@ -229,6 +230,12 @@ __global__ void __launch_bounds__(kSeedThreads) seed_kernel(const Prep* prep, in
     for (int i = threadIdx.x; i < cap; i += blockDim.x) {
         outE[(size_t)blockIdx.x * cap + i] = i < per_block ? E[i] : kEmptyE;
         outC[(size_t)blockIdx.x * cap + i] = i < per_block ? C[i] : kEmptyC;
+    }
+    // the lists are the answer: the records beyond cap must all lie above every candidate window.
+    // The global S-th energy K is at most this block's S-th, so E[cap] > E[S-1] + W suffices.
+    if (hdr && threadIdx.x == 0 && per_block > cap && E[cap] != kEmptyE) {
+        const long long lim = (long long)E[S - 1] + prep->L.W;
+        if ((long long)E[cap] <= lim && prep->L.W > 0) atomicOr(&hdr->status, kErrWindow);
     }
 }
 
@@ -298,12 +305,13 @@ cudaError_t launch_prep(const PrepParams& p, cudaStream_t s)
 
 cudaError_t launch_seed(const Prep* prep, int n, int free_bits, unsigned long long hiconst,
                         unsigned long long sample, int per_block, int blocks, int cap, int* outE,
-                        unsigned long long* outC, cudaStream_t s)
+                        unsigned long long* outC, cudaStream_t s, int S, WsHeader* hdr)
 {
     size_t smem = (size_t)per_block * 12 + (size_t)n * n * 4 + kMaxN * 4;
     cudaError_t e = cudaFuncSetAttribute(seed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    seed_kernel<<<blocks, kSeedThreads, smem, s>>>(prep, n, free_bits, hiconst, sample, per_block, cap, outE, outC);
+    seed_kernel<<<blocks, kSeedThreads, smem, s>>>(prep, n, free_bits, hiconst, sample, per_block, cap, outE, outC,
+                                                   S, hdr);
     count_launches(1);
     return cudaGetLastError();
 }

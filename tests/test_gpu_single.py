@@ -106,6 +106,16 @@ def test_gray_int_pm1(bf, o, n, S, seed):
     check(bf, o, J, h, S)
 
 
+@pytest.mark.parametrize("n,S,seed", [(13, 5, 0), (16, 100, 1), (20, 1000, 2)])
+def test_gray_walk_small_spaces(bf, o, n, S, seed):
+    """Spaces of at most 2^20 configurations are answered by the exact sample alone by default;
+    inner_bits = 9 forces the Gray walk on them."""
+    J, h = rand_float(n, 50 + seed)
+    check(bf, o, J, h, S, inner_bits=9)
+    Ji, hi = rand_pm1(n, 60 + seed)
+    check(bf, o, Ji, hi, S, inner_bits=9)
+
+
 def test_gray_int_wide_range(bf, o):
     rng = np.random.default_rng(21)
     n = 20
@@ -201,17 +211,20 @@ def test_invalid_arguments(bf):
 
 
 def test_spill_overflow_reports_status(bf):
-    """A flood of equal energies into a 16-record spill area must report BF_EOVERFLOW,
-    and the same call with the default area must succeed."""
+    """A flood of equal energies into a 16-record spill area of the walk must report
+    BF_EOVERFLOW, and the same call with the default area must succeed (inner_bits = 9 forces
+    the walk: by default a space of 2^20 configurations is enumerated by the exact sample)."""
     import torch
     from paper_1904_03621_gb300 import _lib
     n = 20
     J = torch.zeros(n, n, dtype=torch.float64, device="cuda")
     h = torch.zeros(n, dtype=torch.float64, device="cuda")
     with pytest.raises(_lib.BFError) as e:
-        bf.low_spectrum(J, h, 10, spill_log2=4)
+        bf.low_spectrum(J, h, 10, spill_log2=4, inner_bits=9)
     assert e.value.status == _lib.BF_EOVERFLOW
-    en, st = bf.low_spectrum(J, h, 10)
+    en, st = bf.low_spectrum(J, h, 10, inner_bits=9)
+    assert bf.states_u64(st).tolist() == list(range(10))
+    en, st = bf.low_spectrum(J, h, 10, spill_log2=4)     # the exact sample needs no spill area
     assert bf.states_u64(st).tolist() == list(range(10))
 
 

@@ -97,7 +97,7 @@ def test_noalloc_reports_device_status_then_recovers(env):
     n = 20
     Jz = torch.zeros(n, n, dtype=torch.int32, device="cuda")
     hz = torch.zeros(n, dtype=torch.int32, device="cuda")
-    status, _, _ = _noalloc(torch, _lib, Jz, hz, 10, _lib.Options(spill_log2=4))
+    status, _, _ = _noalloc(torch, _lib, Jz, hz, 10, _lib.Options(spill_log2=4, inner_bits=9))
     assert status == _lib.BF_EOVERFLOW, _lib.load().bf_last_error_detail().decode()
     J, h = instances.dense_pm1(22, 8)
     Jt = torch.from_numpy(np.ascontiguousarray(J)).cuda()
