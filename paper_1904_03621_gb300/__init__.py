@@ -7,10 +7,10 @@ first use and raise if it is missing.
 import importlib
 
 __all__ = ["instances", "low_spectrum", "low_spectrum_batched", "low_spectrum_backward", "low_spectrum_qubo",
-           "low_spectrum_potts", "LowSpectrumFn", "search", "Solution", "lib"]
+           "low_spectrum_potts", "LowSpectrumFn", "autotune", "fit_spectrum", "search", "Solution", "lib"]
 
 _API = ("low_spectrum", "low_spectrum_batched", "low_spectrum_backward", "low_spectrum_qubo", "low_spectrum_potts",
-        "LowSpectrumFn")
+        "LowSpectrumFn", "autotune")
 
 
 def __getattr__(name):
@@ -18,6 +18,8 @@ def __getattr__(name):
         return importlib.import_module(__name__ + ".instances")
     if name == "lib":
         return importlib.import_module(__name__ + "._lib")
+    if name == "fit_spectrum":
+        return getattr(importlib.import_module(__name__ + ".fit"), name)
     if name in ("search", "Solution", "graph_to_dense"):
         return getattr(importlib.import_module(__name__ + ".graph"), name)
     if name in _API:
