@@ -29,7 +29,10 @@
  * owned by the caller and must stay valid until the work queued on `stream`
  * has completed.  The library never allocates device memory: the caller
  * provides a workspace of at least bf_*_workspace_size() bytes, aligned to
- * 256 bytes.  Calls on one workspace must not overlap in time.
+ * 256 bytes.  Calls on one workspace must not overlap in time.  The library
+ * keeps per-device state for the life of the process (kernel attributes,
+ * events that order its constant tables between streams): after a
+ * cudaDeviceReset() of a device it must not be used on that device again.
  *
  * Errors: argument errors are detected on the host before anything is
  * launched and reported by the return value.  Conditions found on the device
@@ -97,7 +100,7 @@ typedef enum {
  *   inner_bits   spins walked by the fully unrolled block of the Gray-code walk:
  *                0 = automatic (10 for searches of at least 2^42 configurations
  *                and 9 below; spaces of at most 2^20 configurations are then
- *                enumerated exactly by the seed kernel, without a walk), or 9 or
+ *                enumerated exactly by the small-space kernels, without a walk), or 9 or
  *                10 (10 needs n >= 14), which always walks.  Results do not
  *                depend on it.  Ignored by the tensor-core variant.
  * When variant, inner_bits, task_log2 and grid_blocks are all 0 and bf_autotune
@@ -159,7 +162,7 @@ bf_status bf_low_spectrum(const void* J, const void* h, int n, int S, bf_dtype d
  * for one search size by timing candidates on this GPU (CUDA events on
  * `stream`), as the paper chooses its launch configuration by measurement
  * (Sec. 4.2).  Candidates: for spaces of at most 2^20 configurations the
- * exact enumeration by the seed kernel alone (the default there); the
+ * exact small-space enumeration without a walk (the default there); the
  * Gray-code walk with 9 and 10 inner spins, the default task length
  * (task_log2) and lengths 2^2 and 2^4 shorter and 2^2 longer (at most 2^14
  * blocks per task), 1 or 2 blocks per SM; the tensor-core variant with three

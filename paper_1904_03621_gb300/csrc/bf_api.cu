@@ -18,6 +18,22 @@
 namespace bf {
 static std::atomic<long long> g_launches{0};
 void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+static std::mutex g_smem_mutex;
+static std::map<std::pair<int, const void*>, size_t> g_smem_set;   // (device, kernel) -> bytes allowed
+
+cudaError_t ensure_smem(const void* func, size_t bytes)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_smem_mutex);
+    size_t& have = g_smem_set[{dev, func}];
+    if (bytes <= have) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) have = bytes;
+    return e;
+}
 }  // namespace bf
 
 namespace {
@@ -81,7 +97,7 @@ struct Plan {
     int variant;
     int list_cap, grid, m, nh, seg_log2, seed_per_block, seed_blocks, inner_bits;
     int descent_blocks;             // > 0: local-search seed instead of the sampled one
-    bool sample_only;               // the seed enumerates the whole space: its lists are the answer
+    bool sample_only;               // small space: exact enumeration by k_small.cu, no walk
     unsigned long long seed_sample;
     bf::Layout L;
     size_t bytes;
@@ -176,11 +192,11 @@ bf_status make_plan(int n, int S, int dtype, const bf_options* opt, Plan& pl)
     // searches start from the same threshold quality
     pl.seed_per_block = std::max(pl.list_cap, 2048);
     unsigned long long sample = 1ull << std::min(free_bits, bf::kSeedLog2);
-    // spaces of at most 2^20 configurations: the seed evaluates every configuration (exact
-    // energies, one sorted list per seed block) and its merged lists are the answer, so the walk
-    // and its selection are skipped (Gray walk searches with the automatic block size only)
-    pl.sample_only = free_bits <= bf::kSeedLog2 && pl.variant == BF_VARIANT_GRAY && o.inner_bits == 0;
-    if (!pl.sample_only) sample = std::min(sample, (unsigned long long)full_grid * pl.seed_per_block);
+    // spaces of at most 2^20 configurations are enumerated exactly by the small-space kernels
+    // (k_small.cu) instead of seed, walk and merges (Gray walk searches with the automatic block
+    // size only)
+    pl.sample_only = free_bits <= bf::kSmallMaxFreeBits && pl.variant == BF_VARIANT_GRAY && o.inner_bits == 0;
+    sample = std::min(sample, (unsigned long long)full_grid * pl.seed_per_block);
     pl.seed_sample = sample;
     pl.seed_blocks = (int)((sample + pl.seed_per_block - 1) / pl.seed_per_block);
     // beyond 2^kSeedLog2 configurations the sample no longer covers the space: a local search
@@ -188,7 +204,9 @@ bf_status make_plan(int n, int S, int dtype, const bf_options* opt, Plan& pl)
     // spaces the sample's exact S-th energy is much tighter than a ball's: a local search
     // threshold at n = 16..24 made the calls 0.26-0.49 ms instead of 0.22-0.26)
     pl.descent_blocks = free_bits > bf::kSeedLog2 ? std::min(sms, bf::kDescentMaxBlocks) : 0;
-    pl.L = bf::make_layout(S, std::max(pl.grid, pl.seed_blocks), o.spill_log2 ? o.spill_log2 : 21);
+    int lists = std::max(pl.grid, pl.seed_blocks);
+    if (pl.sample_only) lists = std::max(lists, bf::small_lists(free_bits));
+    pl.L = bf::make_layout(S, lists, o.spill_log2 ? o.spill_log2 : 21);
     pl.bytes = pl.L.total;
     return BF_OK;
 }
@@ -327,14 +345,24 @@ bf_status low_spectrum_impl(const void* J, const void* h, int n, int S, bf_dtype
     const int* Wd = &prep->L.W;
     const int* qd = &prep->L.q;
     if (pl.sample_only) {
-        // every configuration evaluated exactly by the seed kernel; the merges keep the S lowest
-        // plus the float window, and a seed block whose dropped records could reach the window
-        // flags BF_EOVERFLOW
-        e = bf::launch_seed(prep, n, pl.free_bits, pl.hiconst, pl.seed_sample, pl.seed_per_block, pl.seed_blocks,
-                            L.list_cap, AE, AC, stream, S, hdr);
-        if (e != cudaSuccess) return cuda_fail(e, "seed kernel");
-        e = merge_tree(AE, AC, BE, BC, pl.seed_blocks, L.list_cap, S, 0, hdr, stream, in_a, Wd);
-        if (e != cudaSuccess) return cuda_fail(e, "seed merge");
+        // small space: every configuration enumerated exactly, 2^13 per block (k_small.cu),
+        // then the merge rounds and the finalising kernels
+        bf::SmallParams sp{};
+        sp.prep = prep;
+        sp.n = n;
+        sp.free_bits = pl.free_bits;
+        sp.S = S;
+        sp.cap = L.list_cap;
+        sp.buf = 8192;
+        sp.nlists = bf::small_lists(pl.free_bits);
+        sp.hiconst = pl.hiconst;
+        sp.list_E = AE;
+        sp.list_C = AC;
+        sp.hdr = hdr;
+        e = bf::launch_small_enum(sp, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "small-space enumeration");
+        e = merge_tree(AE, AC, BE, BC, sp.nlists, L.list_cap, S, 0, hdr, stream, in_a, Wd);
+        if (e != cudaSuccess) return cuda_fail(e, "merge rounds");
         e = bf::launch_finalize(in_a ? AE : BE, in_a ? AC : BC, L.list_cap, S, n, dtype, 0, J, h,
                                 reinterpret_cast<double*>(ws + L.rescore), energies, out_states, hdr, stream, qd);
         if (e != cudaSuccess) return cuda_fail(e, "finalize");
@@ -990,7 +1018,7 @@ extern "C" bf_status bf_autotune(const void* J, const void* h, int n, int S, bf_
     // either side of it, 1 or 2 blocks per SM; the tensor-core variant where it applies
     std::vector<bf_options> cand;
     if (!pl0.direct && pl0.free_bits <= bf::kSeedLog2) {
-        bf_options c = b0;                           // the exact sample of the whole space, no walk
+        bf_options c = b0;                           // the exact small-space enumeration, no walk
         c.variant = BF_VARIANT_GRAY;
         cand.push_back(c);
     }

@@ -323,6 +323,9 @@ int batched_walker_blocks_per_sm();
 
 // Kernels launched by the library (process-wide); every launcher adds its launches.
 void count_launches(int k);
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) only when `bytes` exceeds what was set
+// before for this kernel on the current device (the call costs microseconds per launch)
+cudaError_t ensure_smem(const void* func, size_t bytes);
 // Set the calling thread's error detail (bf_last_error_detail) and return `s`.
 bf_status report(bf_status s, const char* detail);
 
@@ -343,6 +346,23 @@ cudaError_t launch_merge_round(const int* inE, const unsigned long long* inC, in
 cudaError_t launch_absorb_spill(int* E, unsigned long long* C, int nlists, int cap, int S, int W,
                                 const int* spill_E, const unsigned long long* spill_C,
                                 unsigned spill_cap, WsHeader* hdr, cudaStream_t s, const int* Wp = nullptr);
+// Small search spaces (k_small.cu): 2^13 configurations per block of small_enum_kernel (exact
+// Gray enumeration, sorted block list of the S lowest plus the float window).
+constexpr int kSmallBlockBits = 13;
+constexpr int kSmallMaxFreeBits = 20;
+struct SmallParams {
+    const Prep* prep;
+    int n, free_bits, S, cap;
+    int buf;                        // shared-memory records (a power of two >= cap + 4096)
+    int nlists;
+    unsigned long long hiconst;
+    int* list_E;
+    unsigned long long* list_C;
+    WsHeader* hdr;
+};
+int small_lists(int free_bits);
+cudaError_t launch_small_enum(const SmallParams& p, cudaStream_t s);
+
 // Final selection: integer instances write E_q >> q; float instances
 // re-evaluate Eq. (1) in FP64 from the caller's J, h and reselect.
 // qp != nullptr: the scale exponent is read on the device from *qp instead of q.
@@ -351,11 +371,9 @@ cudaError_t launch_finalize(const int* E, const unsigned long long* C, int cap, 
                             void* energies, unsigned long long* states, WsHeader* hdr, cudaStream_t s,
                             const int* qp = nullptr);
 // Seed: `blocks` lists of the lowest sampled records (sample configurations in total).
-// With hdr != nullptr (a sample of the whole space whose lists are the answer), a block whose
-// first dropped record lies within its S-th energy + W flags kErrWindow.
 cudaError_t launch_seed(const Prep* prep, int n, int free_bits, unsigned long long hiconst,
                         unsigned long long sample, int per_block, int blocks, int cap, int* outE,
-                        unsigned long long* outC, cudaStream_t s, int S = 0, WsHeader* hdr = nullptr);
+                        unsigned long long* outC, cudaStream_t s);
 // Local-search seed (k_descent.cu): `blocks` descent blocks, then the S-th lowest distinct
 // energy of the radius-2 Hamming balls around the lowest minima found becomes hdr->tau
 // (assign; needs ball_size(free_bits) >= S) or lowers it (atomicMin).

@@ -58,7 +58,7 @@ cudaError_t launch_backward(const unsigned long long* states, const double* g, c
                             cudaStream_t s)
 {
     size_t smem = (size_t)S * 16;
-    cudaError_t e = cudaFuncSetAttribute(backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem(reinterpret_cast<const void*>(backward_kernel), (size_t)(smem));
     if (e != cudaSuccess) return e;
     backward_kernel<<<B, kBackThreads, smem, s>>>(states, g, n, S, J_off, h_off, dJ, dh, out_f64);
     count_launches(1);

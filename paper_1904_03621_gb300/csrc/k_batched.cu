@@ -991,7 +991,7 @@ int batched_walker_blocks_per_sm()
 {
     int blocks = 0;
     const size_t smem = kBSmem;
-    if (cudaFuncSetAttribute(bwalk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (ensure_smem(reinterpret_cast<const void*>(bwalk_kernel), (size_t)(smem)) != cudaSuccess)
         return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, bwalk_kernel, kBThreads, smem) != cudaSuccess) return 0;
     return blocks;
@@ -1007,14 +1007,14 @@ cudaError_t launch_batched(const BatchParams& p, int walker_grid, cudaStream_t s
     count_launches(1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(bwalk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBSmem);
+    e = ensure_smem(reinterpret_cast<const void*>(bwalk_kernel), (size_t)(kBSmem));
     if (e != cudaSuccess) return e;
     bwalk_kernel<<<walker_grid, kBThreads, kBSmem, s>>>(p);
     count_launches(1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     size_t smem = (size_t)p.final_len * 20;
-    e = cudaFuncSetAttribute(bfinal_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = ensure_smem(reinterpret_cast<const void*>(bfinal_kernel), (size_t)(smem));
     if (e != cudaSuccess) return e;
     bfinal_kernel<<<p.B, kBFinalThreads, smem, s>>>(p);
     count_launches(1);

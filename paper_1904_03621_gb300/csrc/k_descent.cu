@@ -247,14 +247,14 @@ cudaError_t launch_descent_seed(const Prep* prep, int n, int free_bits, unsigned
     if (blocks < 1 || blocks > kDescentMaxBlocks || free_bits > 62 || (assign && ball_size(free_bits) < S))
         return cudaErrorInvalidValue;
     size_t smem = (size_t)n * n * 4;
-    cudaError_t e = cudaFuncSetAttribute(descent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem(reinterpret_cast<const void*>(descent_kernel), (size_t)(smem));
     if (e != cudaSuccess) return e;
     descent_kernel<<<blocks, kDescentThreads, smem, s>>>(prep, n, free_bits, hiconst, bestE, bestC);
     count_launches(1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     size_t bsmem = (size_t)kBallMax * 12 + (size_t)n * n * 4;
-    e = cudaFuncSetAttribute(ball_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsmem);
+    e = ensure_smem(reinterpret_cast<const void*>(ball_kernel), (size_t)(bsmem));
     if (e != cudaSuccess) return e;
     ball_kernel<<<1, kBallThreads, bsmem, s>>>(prep, n, free_bits, S, blocks, bestE, bestC, assign ? 1 : 0, hdr);
     count_launches(1);

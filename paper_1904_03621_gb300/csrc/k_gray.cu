@@ -541,7 +541,7 @@ int gray_blocks_per_sm(int list_cap)
 {
     int blocks = 0;
     size_t smem = gray_smem_bytes(kMaxN, list_cap);
-    if (cudaFuncSetAttribute(gray_kernel<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (ensure_smem(reinterpret_cast<const void*>(gray_kernel<10>), (size_t)(smem)) != cudaSuccess)
         return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, gray_kernel<10>, kGrayThreads, smem) != cudaSuccess)
         return 0;
@@ -552,8 +552,7 @@ template <int IB>
 cudaError_t launch_gray_ib(const GrayParams& p, int grid, cudaStream_t s)
 {
     size_t smem = gray_smem_bytes(p.n, p.list_cap);
-    cudaError_t e = cudaFuncSetAttribute(gray_kernel<IB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)gray_smem_bytes(kMaxN, p.list_cap));
+    cudaError_t e = ensure_smem(reinterpret_cast<const void*>(gray_kernel<IB>), (size_t)(gray_smem_bytes(kMaxN, p.list_cap)));
     if (e != cudaSuccess) return e;
     gray_kernel<IB><<<grid, kGrayThreads, smem, s>>>(p);
     count_launches(1);

@@ -782,7 +782,7 @@ cudaError_t launch_potts_seed(const PottsPrep* prep, int n, int q, unsigned long
                               unsigned long long* outC, cudaStream_t s)
 {
     const size_t smem = (size_t)per_block * 12 + (size_t)n * n * 4 + (size_t)n * q * 4;
-    cudaError_t e = cudaFuncSetAttribute(potts_seed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem(reinterpret_cast<const void*>(potts_seed_kernel), (size_t)(smem));
     if (e != cudaSuccess) return e;
     potts_seed_kernel<<<blocks, kPottsSeedThreads, smem, s>>>(prep, n, q, space, sample, per_block, cap, outE, outC);
     count_launches(1);
@@ -795,7 +795,7 @@ int potts_walk_blocks_per_sm(int q, int m, int n, int list_cap)
     if (q < 3 || q > kPottsMaxQ) return 0;
     const void* fn = walk_for(q);
     const size_t smem = potts_walk_smem(q, n, list_cap);
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    if (ensure_smem(reinterpret_cast<const void*>(fn), (size_t)(smem)) != cudaSuccess) return 0;
     int bps = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kPottsThreads, smem) != cudaSuccess) return 0;
     return bps;
@@ -817,7 +817,7 @@ cudaError_t launch_potts_walk(const PottsParams& p, int grid, cudaStream_t s)
     if (p.q < 3 || p.q > kPottsMaxQ) return cudaErrorInvalidValue;
     const size_t smem = potts_walk_smem(p.q, p.n, p.list_cap);
     const void* fn = walk_for(p.q);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem(reinterpret_cast<const void*>(fn), (size_t)(smem));
     if (e != cudaSuccess) return e;
     int dev = 0;
     e = cudaGetDevice(&dev);
@@ -866,13 +866,12 @@ cudaError_t launch_potts_direct(const void* J, const void* h, int n, int q, int 
     cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), s);
     if (e != cudaSuccess) return e;
     if (dtype == 0) {
-        e = cudaFuncSetAttribute(potts_direct_kernel<long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
+        e = ensure_smem(reinterpret_cast<const void*>(potts_direct_kernel<long long>), (size_t)(smem));
         if (e != cudaSuccess) return e;
         potts_direct_kernel<long long><<<1, kPottsDirectThreads, smem, s>>>(J, h, n, q, dtype, R, S, energies,
                                                                            states);
     } else {
-        e = cudaFuncSetAttribute(potts_direct_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = ensure_smem(reinterpret_cast<const void*>(potts_direct_kernel<double>), (size_t)(smem));
         if (e != cudaSuccess) return e;
         potts_direct_kernel<double><<<1, kPottsDirectThreads, smem, s>>>(J, h, n, q, dtype, R, S, energies, states);
     }
@@ -895,7 +894,7 @@ cudaError_t launch_potts_finalize(const int* E, const unsigned long long* C, int
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem = (size_t)cap * 16;
-    e = cudaFuncSetAttribute(potts_sort_rescored_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = ensure_smem(reinterpret_cast<const void*>(potts_sort_rescored_kernel), (size_t)(smem));
     if (e != cudaSuccess) return e;
     potts_sort_rescored_kernel<<<1, 512, smem, s>>>(C, rescore, cap, S, static_cast<double*>(energies), states);
     count_launches(1);

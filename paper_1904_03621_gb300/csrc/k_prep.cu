@@ -196,8 +196,7 @@ constexpr unsigned long long kSeedMul = 0x9E3779B97F4A7C15ull;
 __global__ void __launch_bounds__(kSeedThreads) seed_kernel(const Prep* prep, int n, int free_bits,
                                                              unsigned long long hiconst,
                                                              unsigned long long sample, int per_block, int cap,
-                                                             int* outE, unsigned long long* outC, int S,
-                                                             WsHeader* hdr)
+                                                             int* outE, unsigned long long* outC)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long* C = reinterpret_cast<unsigned long long*>(smem);   // per_block
@@ -230,12 +229,6 @@ __global__ void __launch_bounds__(kSeedThreads) seed_kernel(const Prep* prep, in
     for (int i = threadIdx.x; i < cap; i += blockDim.x) {
         outE[(size_t)blockIdx.x * cap + i] = i < per_block ? E[i] : kEmptyE;
         outC[(size_t)blockIdx.x * cap + i] = i < per_block ? C[i] : kEmptyC;
-    }
-    // the lists are the answer: the records beyond cap must all lie above every candidate window.
-    // The global S-th energy K is at most this block's S-th, so E[cap] > E[S-1] + W suffices.
-    if (hdr && threadIdx.x == 0 && per_block > cap && E[cap] != kEmptyE) {
-        const long long lim = (long long)E[S - 1] + prep->L.W;
-        if ((long long)E[cap] <= lim && prep->L.W > 0) atomicOr(&hdr->status, kErrWindow);
     }
 }
 
@@ -296,7 +289,7 @@ cudaError_t launch_prep(const PrepParams& p, cudaStream_t s)
 {
     size_t smem = (size_t)p.n * p.n * 8 + kMaxN * 8 + kPrepThreads * 8 + kMaxN * kMaxN * 4 + kMaxN * 4 +
                   kGrayMaxInnerSteps * 4;
-    cudaError_t e = cudaFuncSetAttribute(prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem(reinterpret_cast<const void*>(prep_kernel), (size_t)(smem));
     if (e != cudaSuccess) return e;
     prep_kernel<<<1, kPrepThreads, smem, s>>>(p);
     count_launches(1);
@@ -305,13 +298,12 @@ cudaError_t launch_prep(const PrepParams& p, cudaStream_t s)
 
 cudaError_t launch_seed(const Prep* prep, int n, int free_bits, unsigned long long hiconst,
                         unsigned long long sample, int per_block, int blocks, int cap, int* outE,
-                        unsigned long long* outC, cudaStream_t s, int S, WsHeader* hdr)
+                        unsigned long long* outC, cudaStream_t s)
 {
     size_t smem = (size_t)per_block * 12 + (size_t)n * n * 4 + kMaxN * 4;
-    cudaError_t e = cudaFuncSetAttribute(seed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem(reinterpret_cast<const void*>(seed_kernel), (size_t)(smem));
     if (e != cudaSuccess) return e;
-    seed_kernel<<<blocks, kSeedThreads, smem, s>>>(prep, n, free_bits, hiconst, sample, per_block, cap, outE, outC,
-                                                   S, hdr);
+    seed_kernel<<<blocks, kSeedThreads, smem, s>>>(prep, n, free_bits, hiconst, sample, per_block, cap, outE, outC);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -341,12 +333,12 @@ cudaError_t launch_direct(const void* J, const void* h, int n, int dtype, int S,
     cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), s);
     if (e != cudaSuccess) return e;
     if (dtype == 0) {
-        e = cudaFuncSetAttribute(direct_kernel<long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = ensure_smem(reinterpret_cast<const void*>(direct_kernel<long long>), (size_t)(smem));
         if (e != cudaSuccess) return e;
         direct_kernel<long long><<<1, kDirectThreads, smem, s>>>(J, h, n, dtype, S, free_bits, hiconst, energies, states);
         count_launches(1);
     } else {
-        e = cudaFuncSetAttribute(direct_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = ensure_smem(reinterpret_cast<const void*>(direct_kernel<double>), (size_t)(smem));
         if (e != cudaSuccess) return e;
         direct_kernel<double><<<1, kDirectThreads, smem, s>>>(J, h, n, dtype, S, free_bits, hiconst, energies, states);
         count_launches(1);

@@ -180,7 +180,7 @@ cudaError_t launch_merge_round(const int* inE, const unsigned long long* inC, in
                                const int* Wp)
 {
     size_t smem = (size_t)2 * cap * 12;
-    cudaError_t e = cudaFuncSetAttribute(merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem(reinterpret_cast<const void*>(merge_kernel), (size_t)(smem));
     if (e != cudaSuccess) return e;
     merge_kernel<<<(nin + 1) / 2, kMergeThreads, smem, s>>>(inE, inC, nin, outE, outC, cap, S, W, hdr, Wp);
     count_launches(1);
@@ -192,7 +192,7 @@ cudaError_t launch_absorb_spill(int* E, unsigned long long* C, int nlists, int c
                                 cudaStream_t s, const int* Wp)
 {
     size_t smem = (size_t)2 * cap * 12;
-    cudaError_t e = cudaFuncSetAttribute(absorb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem(reinterpret_cast<const void*>(absorb_kernel), (size_t)(smem));
     if (e != cudaSuccess) return e;
     absorb_kernel<<<nlists, kMergeThreads, smem, s>>>(E, C, nlists, cap, S, W, spill_E, spill_C, spill_cap, hdr, Wp);
     count_launches(1);
@@ -214,7 +214,7 @@ cudaError_t launch_finalize(const int* E, const unsigned long long* C, int cap, 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     size_t smem = (size_t)cap * 16;
-    e = cudaFuncSetAttribute(finalize_float_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = ensure_smem(reinterpret_cast<const void*>(finalize_float_kernel), (size_t)(smem));
     if (e != cudaSuccess) return e;
     finalize_float_kernel<<<1, kMergeThreads, smem, s>>>(C, rescore, cap, S, static_cast<double*>(energies), states);
     count_launches(1);

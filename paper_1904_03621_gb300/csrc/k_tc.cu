@@ -574,7 +574,7 @@ cudaError_t launch_tc(const TcParams& p, int grid, cudaStream_t s)
     // at least 116 KB so that a second block cannot share the SM: each block holds all 512 TMEM columns
     size_t smem = tc_smem_bytes(p.n, p.list_cap);
     if (smem < (size_t)116 * 1024) smem = (size_t)116 * 1024;
-    cudaError_t e = cudaFuncSetAttribute(tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem(reinterpret_cast<const void*>(tc_kernel), (size_t)(smem));
     if (e != cudaSuccess) return e;
     tc_kernel<<<grid, kTcThreads, smem, s>>>(p);
     count_launches(1);

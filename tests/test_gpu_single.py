@@ -108,7 +108,7 @@ def test_gray_int_pm1(bf, o, n, S, seed):
 
 @pytest.mark.parametrize("n,S,seed", [(13, 5, 0), (16, 100, 1), (20, 1000, 2)])
 def test_gray_walk_small_spaces(bf, o, n, S, seed):
-    """Spaces of at most 2^20 configurations are answered by the exact sample alone by default;
+    """Spaces of at most 2^20 configurations are enumerated by the small-space kernels by default;
     inner_bits = 9 forces the Gray walk on them."""
     J, h = rand_float(n, 50 + seed)
     check(bf, o, J, h, S, inner_bits=9)
@@ -213,7 +213,7 @@ def test_invalid_arguments(bf):
 def test_spill_overflow_reports_status(bf):
     """A flood of equal energies into a 16-record spill area of the walk must report
     BF_EOVERFLOW, and the same call with the default area must succeed (inner_bits = 9 forces
-    the walk: by default a space of 2^20 configurations is enumerated by the exact sample)."""
+    the walk: by default a space of 2^20 configurations is enumerated by the small-space kernels)."""
     import torch
     from paper_1904_03621_gb300 import _lib
     n = 20
@@ -224,7 +224,7 @@ def test_spill_overflow_reports_status(bf):
     assert e.value.status == _lib.BF_EOVERFLOW
     en, st = bf.low_spectrum(J, h, 10, inner_bits=9)
     assert bf.states_u64(st).tolist() == list(range(10))
-    en, st = bf.low_spectrum(J, h, 10, spill_log2=4)     # the exact sample needs no spill area
+    en, st = bf.low_spectrum(J, h, 10, spill_log2=4)     # the small-space path needs no spill area
     assert bf.states_u64(st).tolist() == list(range(10))
 
 
