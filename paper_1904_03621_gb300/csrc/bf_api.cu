@@ -318,6 +318,36 @@ bf_status low_spectrum_impl(const void* J, const void* h, int n, int S, bf_dtype
     }
 
     const bf::Layout& L = pl.L;
+    int* AE = reinterpret_cast<int*>(ws + L.listA_E);
+    auto* AC = reinterpret_cast<unsigned long long*>(ws + L.listA_C);
+    int* BE = reinterpret_cast<int*>(ws + L.listB_E);
+    auto* BC = reinterpret_cast<unsigned long long*>(ws + L.listB_C);
+    bool in_a = true;
+
+    if (pl.sample_only) {
+        // small space: the whole search in one kernel, 2^13 configurations enumerated exactly per
+        // block, the block lists merged up a ticketed tree (k_small.cu); list B holds the tickets
+        bf::SmallParams sp{};
+        sp.J = J;
+        sp.h = h;
+        sp.dtype = dtype;
+        sp.n = n;
+        sp.free_bits = pl.free_bits;
+        sp.S = S;
+        sp.cap = L.list_cap;
+        sp.nlists = bf::small_lists(pl.free_bits);
+        sp.hiconst = pl.hiconst;
+        sp.range_flag = range_flag;
+        sp.list_E = AE;
+        sp.list_C = AC;
+        sp.aux = reinterpret_cast<unsigned*>(BE);
+        sp.hdr = hdr;
+        sp.energies = energies;
+        sp.states = out_states;
+        cudaError_t e = bf::launch_small(sp, stream);
+        return e == cudaSuccess ? BF_OK : cuda_fail(e, "small-space search");
+    }
+
     auto* prep = reinterpret_cast<bf::Prep*>(ws + L.prep);
     bf::PrepParams pp{};
     pp.J = J;
@@ -336,39 +366,8 @@ bf_status low_spectrum_impl(const void* J, const void* h, int n, int S, bf_dtype
     cudaError_t e = bf::launch_prep(pp, stream);
     if (e != cudaSuccess) return cuda_fail(e, "prep kernel");
 
-    int* AE = reinterpret_cast<int*>(ws + L.listA_E);
-    auto* AC = reinterpret_cast<unsigned long long*>(ws + L.listA_C);
-    int* BE = reinterpret_cast<int*>(ws + L.listB_E);
-    auto* BC = reinterpret_cast<unsigned long long*>(ws + L.listB_C);
-    bool in_a = true;
-
     const int* Wd = &prep->L.W;
     const int* qd = &prep->L.q;
-    if (pl.sample_only) {
-        // small space: every configuration enumerated exactly, 2^13 per block (k_small.cu),
-        // then the merge rounds and the finalising kernels
-        bf::SmallParams sp{};
-        sp.prep = prep;
-        sp.n = n;
-        sp.free_bits = pl.free_bits;
-        sp.S = S;
-        sp.cap = L.list_cap;
-        sp.buf = 8192;
-        sp.nlists = bf::small_lists(pl.free_bits);
-        sp.hiconst = pl.hiconst;
-        sp.list_E = AE;
-        sp.list_C = AC;
-        sp.hdr = hdr;
-        e = bf::launch_small_enum(sp, stream);
-        if (e != cudaSuccess) return cuda_fail(e, "small-space enumeration");
-        e = merge_tree(AE, AC, BE, BC, sp.nlists, L.list_cap, S, 0, hdr, stream, in_a, Wd);
-        if (e != cudaSuccess) return cuda_fail(e, "merge rounds");
-        e = bf::launch_finalize(in_a ? AE : BE, in_a ? AC : BC, L.list_cap, S, n, dtype, 0, J, h,
-                                reinterpret_cast<double*>(ws + L.rescore), energies, out_states, hdr, stream, qd);
-        if (e != cudaSuccess) return cuda_fail(e, "finalize");
-        if (walked) *walked = (double)(1ull << pl.free_bits);
-        return BF_OK;
-    }
 
     // seed threshold: the S-th lowest quantised energy of a pseudo-random sample, and / or of the
     // Hamming balls around local-search minima (alone when the first ball holds S configurations)

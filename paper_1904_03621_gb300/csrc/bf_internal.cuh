@@ -346,22 +346,29 @@ cudaError_t launch_merge_round(const int* inE, const unsigned long long* inC, in
 cudaError_t launch_absorb_spill(int* E, unsigned long long* C, int nlists, int cap, int S, int W,
                                 const int* spill_E, const unsigned long long* spill_C,
                                 unsigned spill_cap, WsHeader* hdr, cudaStream_t s, const int* Wp = nullptr);
-// Small search spaces (k_small.cu): 2^13 configurations per block of small_enum_kernel (exact
-// Gray enumeration, sorted block list of the S lowest plus the float window).
+// Small search spaces (k_small.cu): the whole search in one launch of small_search_kernel,
+// 2^13 configurations per block (exact Gray enumeration in fixed point), the block lists merged
+// up a ticketed tree, the last block writing the S results.  The kernel quantises the instance
+// itself (the same rule as the preparation kernel), so nothing else runs before it.
 constexpr int kSmallBlockBits = 13;
 constexpr int kSmallMaxFreeBits = 20;
 struct SmallParams {
-    const Prep* prep;
-    int n, free_bits, S, cap;
-    int buf;                        // shared-memory records (a power of two >= cap + 4096)
-    int nlists;
-    unsigned long long hiconst;
-    int* list_E;
+    const void* J;                  // caller's n x n couplings (strict upper triangle read)
+    const void* h;                  // caller's n fields
+    int dtype;                      // 0 int32, 1 float32, 2 float64
+    int n, free_bits, S, cap;       // cap: list capacity, 2 cap <= 2^13
+    int nlists;                     // blocks = 2^(free_bits - 13)
+    unsigned long long hiconst;     // fixed bits of the chunk (Eq. (6))
+    const unsigned* range_flag;     // optional: nonzero marks the instance out of range
+    int* list_E;                    // nlists lists of cap records (the merge tree's nodes)
     unsigned long long* list_C;
+    unsigned* aux;                  // nlists words: status accumulator, then the tree's tickets
     WsHeader* hdr;
+    void* energies;                 // S results: int64 (int32 instances) or float64
+    unsigned long long* states;
 };
 int small_lists(int free_bits);
-cudaError_t launch_small_enum(const SmallParams& p, cudaStream_t s);
+cudaError_t launch_small(const SmallParams& p, cudaStream_t s);
 
 // Final selection: integer instances write E_q >> q; float instances
 // re-evaluate Eq. (1) in FP64 from the caller's J, h and reselect.
