@@ -18,8 +18,10 @@
 //   D[r, c] = sum_i q_i(r) (hi_i(c) + lo_i(c)) + (hi(dQ_o(c)) + lo(dQ_o(c)))
 // with every integer split into two BF16 numbers (K = 7 x 2 + 2 = 16), FP32
 // accumulation in TMEM.  A row is flagged when min_c D[r, c] <= tau - E_base -
-// dR(r) + delta; delta bounds the split residuals (<= 2^-17 |x| each), the FP32
-// accumulation and the conversions (values are below 2^31 in magnitude).  A
+// dR(r) + delta; delta bounds the split residuals (each <= 2^-16 |x|: two roundings to
+// 8 significant bits; the split values of one product sum to less than 2^30 in magnitude,
+// so less than 2^14 in all), the FP32 accumulation and the conversions (partial sums are
+// below 2^31 in magnitude).  A
 // flagged row is rescanned exactly in int32 and only exact hits are recorded.
 // Per outer flip l: E_base += 2 s_l F_l, dR(r) += 4 s_l GR_l(r), dQ(c) += 4 s_l GC_l(c).
 //

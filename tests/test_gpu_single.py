@@ -116,6 +116,22 @@ def test_gray_walk_small_spaces(bf, o, n, S, seed):
     check(bf, o, Ji, hi, S, inner_bits=9)
 
 
+@pytest.mark.parametrize("n,S,seed", [(13, 200, 0), (17, 300, 1), (20, 64, 2)])
+def test_small_space_residual_near_ties(bf, o, n, S, seed):
+    """+-1 couplings and fields perturbed by 1e-6 N(0, 1): the quantisation grid (2^-21 at
+    n = 20) is coarser than the perturbations, so the order of the lowest states is decided by
+    the rounding residuals of the final re-evaluation.  Both the one-launch small-space search
+    and the Gray walk (inner_bits = 9) are compared with the oracle."""
+    rng = np.random.default_rng(90 + seed)
+    J0, h0 = rand_pm1(n, 90 + seed)
+    P = np.triu(rng.standard_normal((n, n)), 1)
+    J = J0.astype(np.float64) + 1e-6 * (P + P.T)
+    h = h0.astype(np.float64) + 1e-6 * rng.standard_normal(n)
+    en, _ = check(bf, o, J, h, S)
+    en9, _ = check(bf, o, J, h, S, inner_bits=9)
+    assert np.abs(en - en9).max() <= 1e-12 * (np.abs(np.triu(J, 1)).sum() + np.abs(h).sum())
+
+
 def test_gray_int_wide_range(bf, o):
     rng = np.random.default_rng(21)
     n = 20
