@@ -21,8 +21,6 @@
 namespace bf {
 
 constexpr int kMaxN = 64;
-constexpr int kInnerBits = 9;                    // spins of the batched preparation's seed walks
-constexpr int kInnerSteps = 1 << kInnerBits;     // configurations per seed walk
 constexpr int kBWalkBits = 9;                    // spins walked inside one unrolled block (batched walker)
 constexpr int kBWalkSteps = 1 << kBWalkBits;     // configurations per block and walk (batched walker)
 constexpr int kGrayMaxInnerBits = 10;            // the same for the single-instance Gray walk (9 or 10)

@@ -37,6 +37,7 @@ constexpr int kBUnitWalkBits = 10;            // a work unit: 2^10 walks (256 th
 constexpr int kBBuf = 1024;                  // records per warp buffer (merged before a 32-record chunk could overflow it)
 constexpr int kBKeepMax = kBBuf / 2;         // records a merged buffer may keep (S plus the float window)
 constexpr int kBSeed = 1024;                  // sampled configurations per instance for its first threshold
+constexpr int kBSampleMaxN = 17;              // largest n whose first threshold uses the sample
 constexpr int kBSeedThreads = 256;
 constexpr int kBDescents = 2;                 // local searches per warp of the preparation block
 constexpr unsigned long long kBDescentSalt = 0x13198A2E03707344ull;
@@ -66,60 +67,6 @@ __device__ double block_sum(double v, double* red)
     return r;
 }
 
-// Seed walks over the 9 inner spins in chunks of 32 Gray steps t = 32 j + i.  For
-// 1 <= i <= 31 the flipped spin is k = ctz(i) <= 4 and its new value is bit k of
-// gray(t) = 1 ^ bit (k+1) of t: known at compile time for k < 4, the parity of j for k = 4.
-// The step entering chunk j >= 1 flips spin 5 + ctz(j).
-static_assert(kInnerBits == 9, "seed walk chunking assumes 9 inner spins");
-
-template <int i>
-__device__ __forceinline__ void seed_step(int& e, int& best, const int (&G)[kInnerBits], const int (&d)[32], bool odd)
-{
-    constexpr int k = cx_ctz(i);
-    int g;
-    if constexpr (k < 4) {
-        constexpr bool up = ((i >> (k + 1)) & 1) == 0;
-        g = up ? G[k] : -G[k];
-    } else {
-        g = odd ? -G[4] : G[4];
-    }
-    e = (int)((unsigned)e + (unsigned)g + (unsigned)d[i]);
-    best = min(best, e);
-}
-
-template <int... Is>
-__device__ __forceinline__ void seed_chunk(int& e, int& best, const int (&G)[kInnerBits], const int (&d)[32], bool odd,
-                                           std::integer_sequence<int, Is...>)
-{
-    (seed_step<Is + 1>(e, best, G, d, odd), ...);
-}
-
-// minimum of the exact energies of the 2^9 configurations of one seed walk (e: energy at g = 0)
-__device__ __forceinline__ void seed_walk(int e, int& best, const int (&G)[kInnerBits], const int* dTx)
-{
-#pragma unroll 1
-    for (int j = 0; j < kInnerSteps / 32; j++) {
-        int d[32];
-        const int4* d4 = reinterpret_cast<const int4*>(dTx + 32 * j);
-#pragma unroll
-        for (int v = 0; v < 8; v++) {
-            const int4 x = d4[v];
-            d[4 * v] = x.x;
-            d[4 * v + 1] = x.y;
-            d[4 * v + 2] = x.z;
-            d[4 * v + 3] = x.w;
-        }
-        if (j > 0) {
-            const int cj = __ffs(j) - 1;                  // spin 5 + cj flips
-            const bool up = ((j >> (cj + 1)) & 1) == 0;
-            const int gk = cj == 0 ? G[5] : cj == 1 ? G[6] : cj == 2 ? G[7] : G[8];
-            e = (int)((unsigned)e + (up ? (unsigned)gk : 0u - (unsigned)gk) + (unsigned)d[0]);
-            best = min(best, e);
-        }
-        seed_chunk(e, best, G, d, (j & 1) != 0, std::make_integer_sequence<int, 31>{});
-    }
-}
-
 // ---- per-instance preparation: one block per instance -----------------------
 
 __global__ void __launch_bounds__(kBSeedThreads, 2) bprep_kernel(const BatchParams p)
@@ -129,9 +76,7 @@ __global__ void __launch_bounds__(kBSeedThreads, 2) bprep_kernel(const BatchPara
     __shared__ double red[kBSeedThreads];
     __shared__ int Jq[kBMaxN * kBMaxN];
     __shared__ int hq[kBMaxN];
-    __shared__ int Tq[kInnerSteps];
-    __shared__ __align__(16) int dTx[kInnerSteps];   // exact T[gray(t)] - T[gray(t-1)]
-    __shared__ int Tw[kBWalkSteps];                  // the walker's inner pair energies (10 spins)
+    __shared__ int Tw[kBWalkSteps];                  // the walker's inner pair energies
     __shared__ int sE[kBSeed];
     __shared__ unsigned long long sC[kBSeed];
     __shared__ int s_q, s_status, s_tau, s_dE[kBSeedThreads / 32], s_F[kBMaxN];
@@ -202,14 +147,6 @@ __global__ void __launch_bounds__(kBSeedThreads, 2) bprep_kernel(const BatchPara
         part += fabs(hd[i] - ldexp(r, -q));
     }
     const double delta = block_sum(part, red);
-    for (int g = tid; g < kInnerSteps; g += blockDim.x) {
-        int t = 0;
-        for (int i = 0; i < kInnerBits; i++) {
-            int si = ((g >> i) & 1) ? 1 : -1;
-            for (int k = i + 1; k < kInnerBits; k++) t += Jq[i * n + k] * si * (((g >> k) & 1) ? 1 : -1);
-        }
-        Tq[g] = t;
-    }
     static_assert(kBWalkBits <= kBMinN, "the walker's inner spins exist in every instance");
     for (int g = tid; g < kBWalkSteps; g += blockDim.x) {
         int t = 0;
@@ -220,72 +157,27 @@ __global__ void __launch_bounds__(kBSeedThreads, 2) bprep_kernel(const BatchPara
         Tw[g] = t;
     }
     __syncthreads();
-    for (int s = tid; s < kInnerSteps; s += blockDim.x) {
-        const int g1 = s ^ (s >> 1), g0 = (s - 1) ^ ((s - 1) >> 1);
-        dTx[s] = s > 0 ? Tq[g1] - Tq[g0] : 0;
-    }
-    __syncthreads();
-    // first threshold.  n >= 18: each of the 256 threads walks its own 2^10 configurations
-    // (low 10 spins free, the rest fixed to a distinct pattern) and keeps the lowest energy;
-    // the S-th lowest of those 256 minima (energies of distinct configurations) bounds the
-    // S-th energy of the instance from above.  The walk is the main walker's
-    // decomposition E(g) = E0 + sum_{k in g} G_k + T[g] - T[0] over the 9 inner spins, twice
-    // (spin 9 at -1, then at +1), one add per configuration.
-    // Smaller n: exact energies of a pseudo-random sample of 1024 (all if fewer).
-    // A local search below may lower the bound.
+    // first threshold.  Spaces of at most 2^17 configurations: the S-th lowest exact energy of a
+    // pseudo-random sample of 1024 configurations (all of them if fewer); the local search below
+    // may lower it.  Larger spaces take the local search's bound alone: a per-thread sampled
+    // walk (256 walks of 2^10 configurations) cost more preparation time than its tighter
+    // start saved in the walker.
     const unsigned long long space = 1ull << n;
-    if (n >= 18) {
-        const unsigned long long hi_mask = (space >> 10) - 1ull;
-        for (int x = tid; x < kBSeed; x += blockDim.x) { sE[x] = kEmptyE; sC[x] = kEmptyC; }
-        __syncthreads();
-        const unsigned long long hi = ((unsigned long long)tid * 0x9E3779B97F4A7C15ull) & hi_mask;
-        unsigned long long c = hi << 10;
+    const int filled = n > kBSampleMaxN ? 0 : (space < (unsigned long long)kBSeed ? (int)space : kBSeed);
+    for (int x = tid; x < kBSeed; x += blockDim.x) {
+        if (x >= filled) { sE[x] = kEmptyE; sC[x] = kEmptyC; continue; }
+        unsigned long long c = (filled == (int)space) ? (unsigned long long)x
+                                                      : (((unsigned long long)x * 0x9E3779B97F4A7C15ull) & (space - 1ull));
         int e = 0;
         for (int i = 0; i < n; i++) {
             int row = hq[i];
             for (int j = i + 1; j < n; j++) row += ((c >> j) & 1ull) ? Jq[i * n + j] : -Jq[i * n + j];
             e += ((c >> i) & 1ull) ? row : -row;
         }
-        // G_k = 2 (h_k + sum_{j >= 9} J_kj s_j), F9 = field of spin 9 (inner spins at -1)
-        int G[kInnerBits];
-#pragma unroll
-        for (int k = 0; k < kInnerBits; k++) {
-            int v = hq[k];
-            for (int j = kInnerBits; j < n; j++) v += ((c >> j) & 1ull) ? Jq[k * n + j] : -Jq[k * n + j];
-            G[k] = 2 * v;
-        }
-        int f9 = hq[kInnerBits];
-        for (int j = 0; j < n; j++) f9 += ((c >> j) & 1ull) ? Jq[kInnerBits * n + j] : -Jq[kInnerBits * n + j];
-        int best = e;
-        seed_walk(e, best, G, dTx);
-        // spin 9 from -1 to +1 (inner spins at -1): E += 2 F9, G_k += 4 J_k9
-        const int e1 = (int)((unsigned)e + ((unsigned)f9 << 1));
-        best = min(best, e1);
-#pragma unroll
-        for (int k = 0; k < kInnerBits; k++) G[k] = (int)((unsigned)G[k] + ((unsigned)Jq[k * n + kInnerBits] << 2));
-        seed_walk(e1, best, G, dTx);
-        const unsigned long long bestc = c;     // distinct per thread: orders equal minima
-        sE[tid] = best;
-        sC[tid] = bestc;
-    } else {
-        const int R = space < (unsigned long long)kBSeed ? (int)space : kBSeed;
-        for (int x = tid; x < kBSeed; x += blockDim.x) {
-            if (x >= R) { sE[x] = kEmptyE; sC[x] = kEmptyC; continue; }
-            unsigned long long c = (R == (int)space) ? (unsigned long long)x
-                                                     : (((unsigned long long)x * 0x9E3779B97F4A7C15ull) & (space - 1ull));
-            int e = 0;
-            for (int i = 0; i < n; i++) {
-                int row = hq[i];
-                for (int j = i + 1; j < n; j++) row += ((c >> j) & 1ull) ? Jq[i * n + j] : -Jq[i * n + j];
-                e += ((c >> i) & 1ull) ? row : -row;
-            }
-            sE[x] = e;
-            sC[x] = c;
-        }
+        sE[x] = e;
+        sC[x] = c;
     }
-    // the seed filled 256 minima (n >= 18) or min(2^n, kBSeed) samples; the rest is empty
     {
-        const int filled = n >= 18 ? kBSeedThreads : (space < (unsigned long long)kBSeed ? (int)space : kBSeed);
         int len = 2;
         while (len < filled || len < p.S) len <<= 1;
         block_sort(sE, sC, len);
@@ -588,6 +480,7 @@ __global__ void __launch_bounds__(kBThreads, 2) bwalk_kernel(const BatchParams p
     __shared__ unsigned long long s_unit;
     __shared__ int s_count[kBWarps];
     __shared__ int s_g[kBWarps][kBWalkBits];          // field row of the walk a warp is rescanning
+    __shared__ int s_fc[kBMaxN], s_Gc[kBWalkBits], s_Ec;   // fields, inner fields, energy at the unit's cc
     const unsigned long long total = *(volatile unsigned long long*)&p.hdr->total_units;
     const int S = p.S;
 
@@ -617,72 +510,97 @@ __global__ void __launch_bounds__(kBThreads, 2) bwalk_kernel(const BatchParams p
         for (int i = threadIdx.x; i < kBMaxN * 16; i += blockDim.x) colq[i / 16][i % 16] = I->col[i / 16][i % 16];
         __syncthreads();
 
+        // The unit's common configuration cc has every task bit that differs between the block's
+        // threads (bits 2..9 of the task index), both walk bits and all inner and middle spins at
+        // -1.  Warp 0 evaluates its local fields and energy once; each thread reaches its first
+        // walk from there by at most 8 flips, and the other three walks by one or two more.
+        const int walk_shift = kBWalkBits + m;
+        const unsigned long long cc = (lu << kBUnitWalkBits) << walk_shift;
+        if (threadIdx.x < 32) {
+            const int i = threadIdx.x;
+            unsigned f = 0u, t2 = 0u;
+            if (i < n) {
+                f = (unsigned)hq[i];                          // f_i = h_i + sum_j J_ij s_j
+                for (int j = 0; j < n; j++) {
+                    const unsigned v = (unsigned)Jq[i * n + j];
+                    f += ((cc >> j) & 1ull) ? v : 0u - v;
+                }
+                const unsigned fh = f + (unsigned)hq[i];
+                t2 = ((cc >> i) & 1ull) ? fh : 0u - fh;      // 2E = sum_i s_i (f_i + h_i)
+                s_fc[i] = (int)f;
+                if (i < kBWalkBits) {
+                    // G_i = 2 (h_i + sum_{j >= inner} J_ij s_j): f_i without the inner spins (all -1)
+                    unsigned gi = f;
+                    for (int j = 0; j < kBWalkBits; j++) gi += (unsigned)Jq[i * n + j];
+                    s_Gc[i] = (int)(gi << 1);
+                }
+            }
+            const unsigned e2 = __reduce_add_sync(0xffffffffu, t2);
+            if (i == 0) s_Ec = (int)e2 >> 1;
+        }
+        __syncthreads();
+
         // walks of this thread: tasks lu * 2^10 + threadIdx.x * 4 + w
         int E0[kWalks], G[kWalks][kBWalkBits], Fm[kWalks][kKeep];
         unsigned long long cfg0[kWalks];
         unsigned active_mask = 0;
-        const int walk_shift = kBWalkBits + m;
         const unsigned long long task0 = (lu << kBUnitWalkBits) + (unsigned long long)(threadIdx.x * kWalks);
 #pragma unroll
         for (int w = 0; w < kWalks; w++)
             if (task0 + (unsigned long long)w < ntasks) active_mask |= 1u << w;
-        cfg0[0] = (active_mask & 1u) ? (task0 << walk_shift) : 0ull;
-        // full O(n^2) state of the first walk; the others differ from it in the two lowest task
-        // spins (walk_shift, walk_shift + 1) and are reached by O(n) flips
+        // an inactive first walk (only in a unit of fewer than 2^10 tasks, where cc = 0) stays at cc
+        const unsigned tb = (active_mask & 1u) ? (unsigned)threadIdx.x : 0u;
+        cfg0[0] = cc | ((unsigned long long)tb << (walk_shift + 2));
+        const int sa = walk_shift, sb = walk_shift + 1;        // the two walk bits
         {
-            const unsigned long long c = cfg0[0];
-            int e = 0;
-            for (int i = 0; i < n; i++) {
-                int row = hq[i];
-                for (int j = i + 1; j < n; j++) row += ((c >> j) & 1ull) ? Jq[i * n + j] : -Jq[i * n + j];
-                e += ((c >> i) & 1ull) ? row : -row;
+            unsigned e = (unsigned)s_Ec;
+            unsigned fa = sa < n ? (unsigned)s_fc[sa] : 0u, fb = sb < n ? (unsigned)s_fc[sb] : 0u;
+            unsigned g0[kBWalkBits], fm0[kKeep];
+#pragma unroll
+            for (int k = 0; k < kBWalkBits; k++) g0[k] = (unsigned)s_Gc[k];
+#pragma unroll
+            for (int r = 0; r < kKeep; r++) fm0[r] = kBWalkBits + r < n ? (unsigned)s_fc[kBWalkBits + r] : 0u;
+            // flip the thread's task spins from -1 to +1 in increasing order: E += 2 f_v, then every
+            // field f_x += 2 J_xv (G_k by 4 J_kv)
+            for (unsigned rest = tb; rest; rest &= rest - 1u) {
+                const int v = walk_shift + 2 + (__ffs(rest) - 1);
+                unsigned fv = (unsigned)s_fc[v];
+                for (unsigned done = tb & ~rest; done; done &= done - 1u)
+                    fv += (unsigned)Jq[(walk_shift + 2 + (__ffs(done) - 1)) * n + v] << 1;
+                e += fv << 1;
+#pragma unroll
+                for (int k = 0; k < kBWalkBits; k++) g0[k] += (unsigned)Jq[k * n + v] << 2;
+#pragma unroll
+                for (int r = 0; r < kKeep; r++)
+                    if (kBWalkBits + r < n) fm0[r] += (unsigned)Jq[(kBWalkBits + r) * n + v] << 1;
+                if (sa < n) fa += (unsigned)Jq[sa * n + v] << 1;
+                if (sb < n) fb += (unsigned)Jq[sb * n + v] << 1;
             }
-            E0[0] = e;
+            E0[0] = (int)e;
 #pragma unroll
-            for (int k = 0; k < kBWalkBits; k++) {
-                int f = hq[k];
-                for (int j = kBWalkBits; j < n; j++) f += ((c >> j) & 1ull) ? Jq[k * n + j] : -Jq[k * n + j];
-                G[0][k] = 2 * f;
-            }
+            for (int k = 0; k < kBWalkBits; k++) G[0][k] = (int)g0[k];
 #pragma unroll
-            for (int r = 0; r < kKeep; r++) {
-                const int l = kBWalkBits + r;
-                int f = l < n ? hq[l] : 0;
-                if (l < n)
-                    for (int j = 0; j < n; j++) f += ((c >> j) & 1ull) ? Jq[l * n + j] : -Jq[l * n + j];
-                Fm[0][r] = f;
-            }
-        }
+            for (int r = 0; r < kKeep; r++) Fm[0][r] = (int)fm0[r];
+            // walk 1 = walk 0 with spin sa up; walk 2 = walk 0 with spin sb up; walk 3 = walk 1 with
+            // spin sb up.  An inactive walk duplicates the walk it is copied from (an active walk's
+            // spins sa / sb exist: its task index has that bit set)
 #pragma unroll
-        for (int w = 1; w < kWalks; w++) {
-            // walk 1 = walk 0 + task bit 0; walk 2 = walk 0 + task bit 1; walk 3 = walk 1 + task bit 1
-            const int from = (w == 3) ? 1 : 0;
-            const int j = walk_shift + ((w == 1) ? 0 : 1);
-            // an inactive walk duplicates the walk it is copied from (state and configuration)
-            cfg0[w] = ((active_mask >> w) & 1u) ? (cfg0[from] ^ (1ull << j)) : cfg0[from];
-            E0[w] = E0[from];
+            for (int w = 1; w < kWalks; w++) {
+                const int from = (w == 3) ? 1 : 0;
+                const int j = (w == 1) ? sa : sb;
+                const bool act = (active_mask >> w) & 1u;
+                cfg0[w] = act ? (cfg0[from] ^ (1ull << j)) : cfg0[from];
+                unsigned fj = (w == 1) ? fa : fb;
+                if (w == 3 && act) fj += (unsigned)Jq[sa * n + sb] << 1;   // field of sb once sa is up
+                E0[w] = act ? (int)((unsigned)E0[from] + (fj << 1)) : E0[from];
 #pragma unroll
-            for (int k = 0; k < kBWalkBits; k++) G[w][k] = G[from][k];
+                for (int k = 0; k < kBWalkBits; k++)
+                    G[w][k] = act ? (int)((unsigned)G[from][k] + ((unsigned)Jq[k * n + j] << 2)) : G[from][k];
 #pragma unroll
-            for (int r = 0; r < kKeep; r++) Fm[w][r] = Fm[from][r];
-            if (j < n && (active_mask >> w) & 1u) {
-                const unsigned long long c = cfg0[from];
-                int f = hq[j];                                  // local field on spin j
-                for (int i = 0; i < n; i++) f += ((c >> i) & 1ull) ? Jq[j * n + i] : -Jq[j * n + i];
-                const bool up = ((c >> j) & 1ull) == 0ull;     // new value of spin j
-                const unsigned dE = (unsigned)f << 1;
-                E0[w] = (int)((unsigned)E0[w] + (up ? dE : 0u - dE));
-#pragma unroll
-                for (int k = 0; k < kBWalkBits; k++) {
-                    const unsigned d = (unsigned)Jq[k * n + j] << 2;
-                    G[w][k] = (int)((unsigned)G[w][k] + (up ? d : 0u - d));
-                }
-#pragma unroll
-                for (int r = 0; r < kKeep; r++) {
-                    const int l = kBWalkBits + r;
-                    const unsigned d = l < n ? (unsigned)Jq[l * n + j] << 1 : 0u;
-                    Fm[w][r] = (int)((unsigned)Fm[w][r] + (up ? d : 0u - d));
-                }
+                for (int r = 0; r < kKeep; r++)
+                    Fm[w][r] = (act && kBWalkBits + r < n)
+                                   ? (int)((unsigned)Fm[from][r] + ((unsigned)Jq[(kBWalkBits + r) * n + j] << 1))
+                                   : Fm[from][r];
             }
         }
         BPacked pk;
@@ -721,14 +639,22 @@ __global__ void __launch_bounds__(kBThreads, 2) bwalk_kernel(const BatchParams p
             pk.Xb = pack_energy(E0[2], E0[3]);
             pk.M[0] = __vminu2(pk.Xa, pk.Xb);
             bwalk_block(pk, reinterpret_cast<const uint4*>(dTw), std::make_integer_sequence<int, kBWalkSteps / 4>{});
-            // bit 2 part + lane: the 16-bit lane (walks 0 and 2 share lane 0, walks 1 and 3 lane 1)
-            // whose minimum over that part of the block reached the threshold
-            unsigned flags = 0u;
+            // one test of the minimum over the whole block first; the per-part flags (bit 2 part +
+            // lane: the 16-bit lane whose minimum over that part reached the threshold; walks 0 and
+            // 2 share lane 0, walks 1 and 3 lane 1) only when some lane of the warp is flagged
+            unsigned mall = pk.M[0];
 #pragma unroll
-            for (int part = 0; part < kBParts; part++)
-                flags |= ((((pk.M[part] & 0xffffu) <= thr16) ? 1u : 0u) | (((pk.M[part] >> 16) <= thr16) ? 2u : 0u))
-                         << (2 * part);
-            const unsigned bal = __ballot_sync(0xffffffffu, flags != 0u);
+            for (int part = 1; part < kBParts; part++) mall = __vminu2(mall, pk.M[part]);
+            const bool hit_any = (mall & 0xffffu) <= thr16 || (mall >> 16) <= thr16;
+            const unsigned bal = __ballot_sync(0xffffffffu, hit_any);
+            unsigned flags = 0u;
+            if (bal) {
+#pragma unroll
+                for (int part = 0; part < kBParts; part++)
+                    flags |= ((((pk.M[part] & 0xffffu) <= thr16) ? 1u : 0u) |
+                              (((pk.M[part] >> 16) <= thr16) ? 2u : 0u))
+                             << (2 * part);
+            }
             if (bal) {
                 // warp-cooperative exact rescan of every flagged walk
                 for (unsigned rest = bal; rest; rest &= rest - 1u) {
