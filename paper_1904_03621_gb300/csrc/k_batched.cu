@@ -38,7 +38,7 @@ constexpr int kBBuf = 1024;                  // records per warp buffer (merged 
 constexpr int kBKeepMax = kBBuf / 2;         // records a merged buffer may keep (S plus the float window)
 constexpr int kBSeed = 1024;                  // sampled configurations per instance for its first threshold
 constexpr int kBSampleMaxN = 17;              // largest n whose first threshold uses the sample
-constexpr int kBSeedThreads = 256;
+constexpr int kBPrepThreads = 256;
 constexpr int kBDescents = 2;                 // local searches per warp of the preparation block
 constexpr unsigned long long kBDescentSalt = 0x13198A2E03707344ull;
 constexpr size_t kBWarpSmem = (size_t)kBBuf * 12;                 // record buffer bytes per warp
@@ -69,18 +69,18 @@ __device__ double block_sum(double v, double* red)
 
 // ---- per-instance preparation: one block per instance -----------------------
 
-__global__ void __launch_bounds__(kBSeedThreads, 2) bprep_kernel(const BatchParams p)
+__global__ void __launch_bounds__(kBPrepThreads, 2) bprep_kernel(const BatchParams p)
 {
     __shared__ double Jd[kBMaxN * kBMaxN];
     __shared__ double hd[kBMaxN];
-    __shared__ double red[kBSeedThreads];
+    __shared__ double red[kBPrepThreads];
     __shared__ int Jq[kBMaxN * kBMaxN];
     __shared__ int hq[kBMaxN];
     __shared__ int Tw[kBWalkSteps];                  // the walker's inner pair energies
     __shared__ int sE[kBSeed];
     __shared__ unsigned long long sC[kBSeed];
-    __shared__ int s_q, s_status, s_tau, s_dE[kBSeedThreads / 32], s_F[kBMaxN];
-    __shared__ unsigned long long s_dC[kBSeedThreads / 32];
+    __shared__ int s_q, s_status, s_tau, s_dE[kBPrepThreads / 32], s_F[kBMaxN];
+    __shared__ unsigned long long s_dC[kBPrepThreads / 32];
     __shared__ double s_emax;
 
     const int b = blockIdx.x, tid = threadIdx.x;
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(kBSeedThreads, 2) bprep_kernel(const BatchPara
         int bE = kEmptyE;
         unsigned long long bC = kEmptyC;
         for (int r = 0; r < kBDescents; r++) {
-            const unsigned long long id = ((unsigned long long)b * (kBSeedThreads / 32) + warp) * kBDescents + r;
+            const unsigned long long id = ((unsigned long long)b * (kBPrepThreads / 32) + warp) * kBDescents + r;
             unsigned long long c = splitmix64(kBDescentSalt + id) & (space - 1ull);
             unsigned f = 0u;
             if (lane < n) {
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(kBSeedThreads, 2) bprep_kernel(const BatchPara
         if (lane == 0) { s_dE[warp] = bE; s_dC[warp] = bC; }
         __syncthreads();
         if (tid == 0) {
-            for (int w2 = 1; w2 < kBSeedThreads / 32; w2++)
+            for (int w2 = 1; w2 < kBPrepThreads / 32; w2++)
                 if (rec_less(s_dE[w2], s_dC[w2], s_dE[0], s_dC[0])) { s_dE[0] = s_dE[w2]; s_dC[0] = s_dC[w2]; }
         }
         __syncthreads();
@@ -925,7 +925,7 @@ int batched_walker_blocks_per_sm()
 
 cudaError_t launch_batched(const BatchParams& p, int walker_grid, cudaStream_t s)
 {
-    bprep_kernel<<<p.B, kBSeedThreads, 0, s>>>(p);
+    bprep_kernel<<<p.B, kBPrepThreads, 0, s>>>(p);
     count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
