@@ -289,7 +289,12 @@ struct BInst {                                   // per-instance constants (devi
     int T[kBWalkSteps];                          // inner pair energies of the walker's block
     unsigned dT16[kBWalkSteps];
     int col[kBMaxN][16];
+    // float instances: rounding residuals rho = x - x_q 2^-q as integers round(rho 2^(q+48))
+    // (J: strict upper triangle, row stride n; h), for the final re-evaluation of Eq. (1)
+    long long R[kBMaxN * kBMaxN];
+    long long Rh[kBMaxN];
 };
+constexpr int kBResBits = 48;                    // fixed-point scale of BInst::R, Rh: 2^(q+48)
 
 struct BatchParams {
     int B, n_max, S, dtype, m_cap, pool_cap, final_len, pad0;

@@ -54,17 +54,66 @@ __device__ __forceinline__ double load_value(const void* p, int dtype, size_t id
     return static_cast<const double*>(p)[idx];
 }
 
+// sum over the block: warp shuffles, then one warp over the per-warp partial sums
 __device__ double block_sum(double v, double* red)
 {
-    red[threadIdx.x] = v;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) red[warp] = v;
     __syncthreads();
-    for (int s = blockDim.x >> 1; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-        __syncthreads();
+    if (warp == 0) {
+        double t = lane < nw ? red[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) red[32] = t;
     }
-    double r = red[0];
+    __syncthreads();
+    const double r = red[32];
     __syncthreads();
     return r;
+}
+
+// The k-th lowest (1 <= k <= kBMaxS) of the values the block's threads hold, kPer per thread
+// (kEmptyE pads; kEmptyE when fewer than k are real).  Each warp extracts its k lowest by
+// repeated warp minima, then warp 0 extracts the k-th lowest of the 8 sorted warp lists: two
+// block barriers instead of a block-wide sort.
+constexpr int kBPer = 4;                       // values per thread of kth_lowest
+__device__ int kth_lowest(int (&v)[kBPer], int k, int* lists /* kBPrepThreads / 32 * kBMaxS */, int* out)
+{
+    // sort the thread's values ascending (insertion)
+#pragma unroll
+    for (int a = 1; a < kBPer; a++)
+#pragma unroll
+        for (int c = a; c > 0; c--)
+            if (v[c] < v[c - 1]) { const int t = v[c]; v[c] = v[c - 1]; v[c - 1] = t; }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int* L = lists + warp * kBMaxS;
+    for (int r = 0; r < k; r++) {
+        const int m = __reduce_min_sync(0xffffffffu, v[0]);
+        const unsigned own = __ballot_sync(0xffffffffu, v[0] == m);
+        if (lane == __ffs(own) - 1) {
+#pragma unroll
+            for (int a = 0; a + 1 < kBPer; a++) v[a] = v[a + 1];
+            v[kBPer - 1] = kEmptyE;
+        }
+        if (lane == 0) L[r] = m;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        constexpr int nw = kBPrepThreads / 32;
+        int pos = 0, head = lane < nw ? lists[lane * kBMaxS] : kEmptyE, kth = kEmptyE;
+        for (int r = 0; r < k; r++) {
+            const int m = __reduce_min_sync(0xffffffffu, head);
+            const unsigned own = __ballot_sync(0xffffffffu, head == m);
+            if (lane == __ffs(own) - 1) {
+                ++pos;
+                head = pos < k ? lists[lane * kBMaxS + pos] : kEmptyE;
+            }
+            kth = m;
+        }
+        if (lane == 0) *out = kth;
+    }
+    __syncthreads();
+    return *out;
 }
 
 // ---- per-instance preparation: one block per instance -----------------------
@@ -73,12 +122,11 @@ __global__ void __launch_bounds__(kBPrepThreads, 2) bprep_kernel(const BatchPara
 {
     __shared__ double Jd[kBMaxN * kBMaxN];
     __shared__ double hd[kBMaxN];
-    __shared__ double red[kBPrepThreads];
+    __shared__ double red[33];
     __shared__ int Jq[kBMaxN * kBMaxN];
     __shared__ int hq[kBMaxN];
     __shared__ int Tw[kBWalkSteps];                  // the walker's inner pair energies
-    __shared__ int sE[kBSeed];
-    __shared__ unsigned long long sC[kBSeed];
+    __shared__ int s_lists[kBPrepThreads / 32 * kBMaxS], s_kth;   // kth_lowest's warp lists
     __shared__ int s_q, s_status, s_tau, s_dE[kBPrepThreads / 32], s_F[kBMaxN];
     __shared__ unsigned long long s_dC[kBPrepThreads / 32];
     __shared__ double s_emax;
@@ -98,15 +146,18 @@ __global__ void __launch_bounds__(kBPrepThreads, 2) bprep_kernel(const BatchPara
         return;
     }
     const long long jo = p.J_off[b], ho = p.h_off[b];
-    for (int idx = tid; idx < n * n; idx += blockDim.x) {
-        int i = idx / n, j = idx % n;
-        Jd[idx] = (i < j) ? load_value(p.J, p.dtype, jo + idx) : 0.0;
-    }
-    for (int i = tid; i < n; i += blockDim.x) hd[i] = load_value(p.h, p.dtype, ho + i);
-    __syncthreads();
+    // one row of J per warp at a time, lane j = column j (n <= 32): the strict upper triangle
+    const int lane = tid & 31, warp = tid >> 5;
     double part = 0.0;
-    for (int idx = tid; idx < n * n; idx += blockDim.x) part += fabs(Jd[idx]);
-    for (int i = tid; i < n; i += blockDim.x) part += fabs(hd[i]);
+    for (int i = warp; i < n; i += kBPrepThreads / 32) {
+        const double x = (lane < n && i < lane) ? load_value(p.J, p.dtype, jo + (long long)i * n + lane) : 0.0;
+        if (lane < n) Jd[i * n + lane] = x;
+        part += fabs(x);
+    }
+    if (warp == 0 && lane < n) {
+        hd[lane] = load_value(p.h, p.dtype, ho + lane);
+        part += fabs(hd[lane]);
+    }
     const double emax = block_sum(part, red);
     if (tid == 0) {
         int status = 0, q = 0;
@@ -128,25 +179,33 @@ __global__ void __launch_bounds__(kBPrepThreads, 2) bprep_kernel(const BatchPara
     }
     __syncthreads();
     const int q = s_q;
+    // J_q = rint(J 2^q), h_q = rint(h 2^q); 2^q is a power of two, so x 2^q is exact and so is
+    // its distance to the rounded integer: the residual sum is accumulated in quantised units
+    const double scale = ldexp(1.0, q);
     part = 0.0;
-    for (int idx = tid; idx < n * n; idx += blockDim.x) {
-        int i = idx / n, j = idx % n;
-        int a = i < j ? i : j, c = i < j ? j : i;
-        int v = 0;
-        if (a != c) {
-            double x = Jd[a * n + c];
-            double r = rint(ldexp(x, q));
-            v = (int)r;
-            if (i < j) part += fabs(x - ldexp(r, -q));
+    for (int i = warp; i < n; i += kBPrepThreads / 32) {
+        if (lane < n) {
+            int v = 0;
+            if (i < lane) {
+                const double t = Jd[i * n + lane] * scale;
+                const double r = rint(t);
+                v = (int)r;
+                part += fabs(t - r);
+                // rho 2^(q+48) = (t - r) 2^48: t - r is exact (Sterbenz), the scaling too
+                if (p.dtype != 0) I->R[i * n + lane] = __double2ll_rn(ldexp(t - r, kBResBits));
+            }
+            if (i <= lane) Jq[i * n + lane] = v;   // strict upper triangle and the diagonal (0)
+            if (i < lane) Jq[lane * n + i] = v;    // mirrored into the lower triangle
         }
-        Jq[idx] = v;
     }
-    for (int i = tid; i < n; i += blockDim.x) {
-        double r = rint(ldexp(hd[i], q));
-        hq[i] = (int)r;
-        part += fabs(hd[i] - ldexp(r, -q));
+    if (warp == 0 && lane < n) {
+        const double t = hd[lane] * scale;
+        const double r = rint(t);
+        hq[lane] = (int)r;
+        part += fabs(t - r);
+        if (p.dtype != 0) I->Rh[lane] = __double2ll_rn(ldexp(t - r, kBResBits));
     }
-    const double delta = block_sum(part, red);
+    const double delta = ldexp(block_sum(part, red), -q);
     static_assert(kBWalkBits <= kBMinN, "the walker's inner spins exist in every instance");
     for (int g = tid; g < kBWalkSteps; g += blockDim.x) {
         int t = 0;
@@ -164,25 +223,28 @@ __global__ void __launch_bounds__(kBPrepThreads, 2) bprep_kernel(const BatchPara
     // start saved in the walker.
     const unsigned long long space = 1ull << n;
     const int filled = n > kBSampleMaxN ? 0 : (space < (unsigned long long)kBSeed ? (int)space : kBSeed);
-    for (int x = tid; x < kBSeed; x += blockDim.x) {
-        if (x >= filled) { sE[x] = kEmptyE; sC[x] = kEmptyC; continue; }
-        unsigned long long c = (filled == (int)space) ? (unsigned long long)x
-                                                      : (((unsigned long long)x * 0x9E3779B97F4A7C15ull) & (space - 1ull));
-        int e = 0;
-        for (int i = 0; i < n; i++) {
-            int row = hq[i];
-            for (int j = i + 1; j < n; j++) row += ((c >> j) & 1ull) ? Jq[i * n + j] : -Jq[i * n + j];
-            e += ((c >> i) & 1ull) ? row : -row;
-        }
-        sE[x] = e;
-        sC[x] = c;
-    }
+    static_assert(kBSeed == kBPer * kBPrepThreads, "the sample is kBPer configurations per thread");
     {
-        int len = 2;
-        while (len < filled || len < p.S) len <<= 1;
-        block_sort(sE, sC, len);
+        int ev[kBPer];
+#pragma unroll
+        for (int a = 0; a < kBPer; a++) {
+            const int x = tid + a * kBPrepThreads;
+            ev[a] = kEmptyE;
+            if (x >= filled) continue;
+            const unsigned long long c = (filled == (int)space) ? (unsigned long long)x
+                                                                : (((unsigned long long)x * 0x9E3779B97F4A7C15ull) & (space - 1ull));
+            int e = 0;
+            for (int i = 0; i < n; i++) {
+                int row = hq[i];
+                for (int j = i + 1; j < n; j++) row += ((c >> j) & 1ull) ? Jq[i * n + j] : -Jq[i * n + j];
+                e += ((c >> i) & 1ull) ? row : -row;
+            }
+            ev[a] = e;
+        }
+        // the S-th lowest sampled energy (of distinct configurations) bounds the S-th energy
+        const int t = kth_lowest(ev, p.S, s_lists, &s_kth);
+        if (tid == 0) s_tau = t;
     }
-    if (tid == 0) s_tau = sE[p.S - 1];
 
     // A second bound from a local search (n > 10; smaller spaces were enumerated above):
     // each warp runs steepest-descent searches from pseudo-random starts, lane l holding the
@@ -244,17 +306,18 @@ __global__ void __launch_bounds__(kBPrepThreads, 2) bprep_kernel(const BatchPara
         }
         __syncthreads();
         // slot x: 0 = the minimum, 1..n single flips, then the pairs i < j in row order
-        int blen = 2;
-        while (blen < ball) blen <<= 1;
-        for (int x = tid; x < blen; x += blockDim.x) {
-            if (x >= ball) { sE[x] = kEmptyE; sC[x] = kEmptyC; continue; }
+        static_assert(1 + kBMaxN + kBMaxN * (kBMaxN - 1) / 2 <= kBPer * kBPrepThreads, "ball slots per thread");
+        int ev[kBPer];
+#pragma unroll
+        for (int a = 0; a < kBPer; a++) {
+            const int x = tid + a * kBPrepThreads;
+            ev[a] = kEmptyE;
+            if (x >= ball) continue;
             unsigned e = (unsigned)E0;
-            unsigned long long cx = c0;
             if (x >= 1 && x <= n) {
                 const int i = x - 1;
                 const unsigned sf = ((c0 >> i) & 1ull) ? (unsigned)s_F[i] : 0u - (unsigned)s_F[i];
                 e -= sf << 1;
-                cx ^= 1ull << i;
             } else if (x > n) {
                 int pr = x - 1 - n, i = 0;
                 while (pr >= n - 1 - i) { pr -= n - 1 - i; i++; }
@@ -264,13 +327,11 @@ __global__ void __launch_bounds__(kBPrepThreads, 2) bprep_kernel(const BatchPara
                 const unsigned fj = sj ? (unsigned)s_F[j] : 0u - (unsigned)s_F[j];
                 const unsigned jij = (unsigned)Jq[i * n + j] << 2;
                 e = e - (fi << 1) - (fj << 1) + (si == sj ? jij : 0u - jij);
-                cx ^= (1ull << i) | (1ull << j);
             }
-            sE[x] = (int)e;
-            sC[x] = cx;
+            ev[a] = (int)e;
         }
-        block_sort(sE, sC, blen);
-        if (tid == 0 && sE[p.S - 1] < s_tau) s_tau = sE[p.S - 1];
+        const int t = kth_lowest(ev, p.S, s_lists, &s_kth);
+        if (tid == 0 && t < s_tau) s_tau = t;
     }
     __syncthreads();
     // outputs
@@ -877,29 +938,35 @@ __global__ void __launch_bounds__(kBFinalThreads) bfinal_kernel(const BatchParam
         }
         return;
     }
-    // FP64 re-evaluation of Eq. (1) for the kept records, then reselection by (E, c)
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const long long jo = p.J_off[b], ho = p.h_off[b];
+    // Re-evaluation of Eq. (1) for the kept records, then reselection by (E, c).  Eq. (1)
+    // splits into the quantised energy and the rounding residuals, E(c) = 2^-q (E_q(c) + R(c)),
+    // R(c) = sum_{i<j} rho_ij s_i s_j + sum_i rho_i s_i, summed exactly in 64-bit fixed point
+    // (scale 2^(q+48), |rho'| <= 2^47 per term, at most 528 terms), then rounded once to FP64.
+    // The residuals' truncation to that scale, at most 2^-(q+38) in all, lies far below the FP64
+    // unit of E (emax 2^-29 ~ 2^-q).  Integer arithmetic instead of an FP64 sum per record: the
+    // FP64 unit of this GPU issues 2 lanes per clock per SM.
+    long long* Rs = reinterpret_cast<long long*>(E64 + len);   // n x n (row stride n), then h
+    for (int x = threadIdx.x; x < n * n; x += blockDim.x) Rs[x] = (x % n > x / n) ? I->R[x] : 0ll;
+    for (int x = threadIdx.x; x < n; x += blockDim.x) Rs[n * n + x] = I->Rh[x];
     int lenk = 2;                                      // a power of two >= max(keep, S), <= lenb
     while (lenk < keep || lenk < S) lenk <<= 1;
     if (lenk > lenb) lenk = lenb;
-    for (int r = warp; r < lenk; r += nw) {
+    __syncthreads();
+    const double sq = ldexp(1.0, -I->q), sr = ldexp(1.0, -I->q - kBResBits);
+    for (int r = threadIdx.x; r < lenk; r += blockDim.x) {
         if (r >= keep) {
-            if (lane == 0) E64[r] = DBL_MAX;
+            E64[r] = DBL_MAX;
             continue;
         }
         const unsigned long long c = C[r];
-        double part = 0.0;
-        for (int i = lane; i < n; i += 32) {
-            double row = load_value(p.h, p.dtype, ho + i);
-            for (int j = i + 1; j < n; j++) {
-                double v = load_value(p.J, p.dtype, jo + (long long)i * n + j);
-                row += ((c >> j) & 1ull) ? v : -v;
-            }
-            part += ((c >> i) & 1ull) ? row : -row;
+        long long R = 0;
+        for (int i = 0; i < n; i++) {
+            long long row = Rs[n * n + i];
+            const long long* Ri = Rs + i * n;
+            for (int j = i + 1; j < n; j++) row += ((c >> j) & 1ull) ? Ri[j] : -Ri[j];
+            R += ((c >> i) & 1ull) ? row : -row;
         }
-        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        if (lane == 0) E64[r] = part;
+        E64[r] = (double)E[r] * sq + (double)R * sr;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < lenk; i += blockDim.x)
@@ -939,7 +1006,7 @@ cudaError_t launch_batched(const BatchParams& p, int walker_grid, cudaStream_t s
     count_launches(1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    size_t smem = (size_t)p.final_len * 20;
+    size_t smem = (size_t)p.final_len * 20 + (size_t)(kBMaxN * kBMaxN + kBMaxN) * 8;
     e = ensure_smem(reinterpret_cast<const void*>(bfinal_kernel), (size_t)(smem));
     if (e != cudaSuccess) return e;
     bfinal_kernel<<<p.B, kBFinalThreads, smem, s>>>(p);
