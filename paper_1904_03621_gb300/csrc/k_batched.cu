@@ -37,7 +37,7 @@ constexpr int kBUnitWalkBits = 10;            // a work unit: 2^10 walks (256 th
 constexpr int kBBuf = 1024;                  // records per warp buffer (merged before a 32-record chunk could overflow it)
 constexpr int kBKeepMax = kBBuf / 2;         // records a merged buffer may keep (S plus the float window)
 constexpr int kBSeed = 1024;                  // sampled configurations per instance for its first threshold
-constexpr int kBSampleMaxN = 17;              // largest n whose first threshold uses the sample
+constexpr int kBSampleMaxN = 10;              // largest n whose first threshold uses the sample
 constexpr int kBPrepThreads = 256;
 constexpr int kBDescents = 2;                 // local searches per warp of the preparation block
 constexpr unsigned long long kBDescentSalt = 0x13198A2E03707344ull;
@@ -118,7 +118,7 @@ __device__ int kth_lowest(int (&v)[kBPer], int k, int* lists /* kBPrepThreads / 
 
 // ---- per-instance preparation: one block per instance -----------------------
 
-__global__ void __launch_bounds__(kBPrepThreads, 2) bprep_kernel(const BatchParams p)
+__global__ void __launch_bounds__(kBPrepThreads, 4) bprep_kernel(const BatchParams p)
 {
     __shared__ double Jd[kBMaxN * kBMaxN];
     __shared__ double hd[kBMaxN];
@@ -216,11 +216,10 @@ __global__ void __launch_bounds__(kBPrepThreads, 2) bprep_kernel(const BatchPara
         Tw[g] = t;
     }
     __syncthreads();
-    // first threshold.  Spaces of at most 2^17 configurations: the S-th lowest exact energy of a
-    // pseudo-random sample of 1024 configurations (all of them if fewer); the local search below
-    // may lower it.  Larger spaces take the local search's bound alone: a per-thread sampled
-    // walk (256 walks of 2^10 configurations) cost more preparation time than its tighter
-    // start saved in the walker.
+    // first threshold.  n = 10: the S-th lowest of all 1024 exact energies.  Larger spaces take
+    // the local search's bound below: a per-thread sampled walk (256 walks of 2^10
+    // configurations) or an exact sample of 1024 configurations cost more preparation time
+    // than their tighter start saved in the walker.
     const unsigned long long space = 1ull << n;
     const int filled = n > kBSampleMaxN ? 0 : (space < (unsigned long long)kBSeed ? (int)space : kBSeed);
     static_assert(kBSeed == kBPer * kBPrepThreads, "the sample is kBPer configurations per thread");
@@ -253,7 +252,6 @@ __global__ void __launch_bounds__(kBPrepThreads, 2) bprep_kernel(const BatchPara
     // of the best minimum bounds the S-th energy too; the lower of the two bounds is kept.
     const int ball = 1 + n + n * (n - 1) / 2;
     if (n > 10 && ball >= p.S) {
-        const int lane = tid & 31, warp = tid >> 5;
         int bE = kEmptyE;
         unsigned long long bC = kEmptyC;
         for (int r = 0; r < kBDescents; r++) {
@@ -305,30 +303,28 @@ __global__ void __launch_bounds__(kBPrepThreads, 2) bprep_kernel(const BatchPara
             s_F[tid] = (int)f;
         }
         __syncthreads();
-        // slot x: 0 = the minimum, 1..n single flips, then the pairs i < j in row order
-        static_assert(1 + kBMaxN + kBMaxN * (kBMaxN - 1) / 2 <= kBPer * kBPrepThreads, "ball slots per thread");
+        // slots on a 32 x 32 grid, row i = warp + 8 a, column j = lane: (i, i) flips spin i,
+        // (i, j) with i < j flips spins i and j, and (1, 0) is the minimum itself
+        static_assert(kBPer * kBPrepThreads == kBMaxN * kBMaxN && kBPrepThreads == 8 * 32, "ball grid");
         int ev[kBPer];
 #pragma unroll
         for (int a = 0; a < kBPer; a++) {
-            const int x = tid + a * kBPrepThreads;
+            const int i = warp + 8 * a, j = lane;
             ev[a] = kEmptyE;
-            if (x >= ball) continue;
-            unsigned e = (unsigned)E0;
-            if (x >= 1 && x <= n) {
-                const int i = x - 1;
-                const unsigned sf = ((c0 >> i) & 1ull) ? (unsigned)s_F[i] : 0u - (unsigned)s_F[i];
-                e -= sf << 1;
-            } else if (x > n) {
-                int pr = x - 1 - n, i = 0;
-                while (pr >= n - 1 - i) { pr -= n - 1 - i; i++; }
-                const int j = i + 1 + pr;
-                const bool si = (c0 >> i) & 1ull, sj = (c0 >> j) & 1ull;
+            if (i == 1 && j == 0) {
+                ev[a] = E0;
+            } else if (i < n && j < n && i <= j) {
+                const bool si = (c0 >> i) & 1ull;
                 const unsigned fi = si ? (unsigned)s_F[i] : 0u - (unsigned)s_F[i];
-                const unsigned fj = sj ? (unsigned)s_F[j] : 0u - (unsigned)s_F[j];
-                const unsigned jij = (unsigned)Jq[i * n + j] << 2;
-                e = e - (fi << 1) - (fj << 1) + (si == sj ? jij : 0u - jij);
+                unsigned e = (unsigned)E0 - (fi << 1);
+                if (i < j) {
+                    const bool sj = (c0 >> j) & 1ull;
+                    const unsigned fj = sj ? (unsigned)s_F[j] : 0u - (unsigned)s_F[j];
+                    const unsigned jij = (unsigned)Jq[i * n + j] << 2;
+                    e = e - (fj << 1) + (si == sj ? jij : 0u - jij);
+                }
+                ev[a] = (int)e;
             }
-            ev[a] = (int)e;
         }
         const int t = kth_lowest(ev, p.S, s_lists, &s_kth);
         if (tid == 0 && t < s_tau) s_tau = t;
