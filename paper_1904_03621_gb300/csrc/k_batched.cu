@@ -888,7 +888,7 @@ namespace {
 
 // ---- per-instance final selection: one block per instance -----------------------
 
-constexpr int kBFinalThreads = 512;
+constexpr int kBFinalThreads = 128;
 
 __global__ void __launch_bounds__(kBFinalThreads) bfinal_kernel(const BatchParams p)
 {
