@@ -207,13 +207,18 @@ __global__ void __launch_bounds__(kBPrepThreads, 4) bprep_kernel(const BatchPara
     }
     const double delta = ldexp(block_sum(part, red), -q);
     static_assert(kBWalkBits <= kBMinN, "the walker's inner spins exist in every instance");
-    for (int g = tid; g < kBWalkSteps; g += blockDim.x) {
-        int t = 0;
-        for (int i = 0; i < kBWalkBits; i++) {
-            int si = ((g >> i) & 1) ? 1 : -1;
-            for (int k = i + 1; k < kBWalkBits; k++) t += Jq[i * n + k] * si * (((g >> k) & 1) ? 1 : -1);
+    // inner pair energies T[g] = sum_{i<k} J_ik s_i s_k over the walker's inner spins: the pairs
+    // below the top inner spin by the definition, then T = t -+ f_top for the top spin at -1 / +1
+    constexpr int kHalf = kBWalkSteps / 2, kTop = kBWalkBits - 1;
+    for (int g = tid; g < kHalf; g += blockDim.x) {
+        int t = 0, ft = 0;
+        for (int i = 0; i < kTop; i++) {
+            const int si = ((g >> i) & 1) ? 1 : -1;
+            for (int k = i + 1; k < kTop; k++) t += Jq[i * n + k] * si * (((g >> k) & 1) ? 1 : -1);
+            ft += Jq[i * n + kTop] * si;
         }
-        Tw[g] = t;
+        Tw[g] = t - ft;
+        Tw[g + kHalf] = t + ft;
     }
     __syncthreads();
     // first threshold.  n = 10: the S-th lowest of all 1024 exact energies.  Larger spaces take
