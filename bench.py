@@ -834,7 +834,10 @@ def main():
         "autotuned": tuned,
     }
     if not args.no_batched:
-        line["batched"] = batched_section(api, torch, dev, max(args.steps, 3), max(args.warmup, 3))
+        bsec = batched_section(api, torch, dev, max(args.steps, 3), max(args.warmup, 3))
+        # the whole batched call (preparation, walk, final selection) against the walk's issue peak
+        bsec["issue_roofline_frac"] = bsec["configs_per_s"] * ALU_OPS_PER_CONFIG / peak_ops
+        line["batched"] = bsec
         line["configs"] = config_checks(api, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(J, h, S)
