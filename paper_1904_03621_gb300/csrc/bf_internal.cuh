@@ -203,6 +203,7 @@ struct TcParams {                   // tensor-core screening kernel (k_tc.cu); W
 constexpr int kPottsMinQ = 2, kPottsMaxQ = 8;
 constexpr int kPottsMaxSteps = 1024;              // configurations of one inner block (q^B)
 constexpr int kPottsMidTable = 16;                // max m * q (per-walk middle-digit tables)
+constexpr int kPottsMaxBlocks = 256;              // q^m <= 256 blocks per task when m * q <= 16
 constexpr int kPottsWalks = 2;                    // walks per thread: two 16-bit lanes of one register
 
 // inner digits walked by the unrolled block for q states (q^B <= kPottsMaxSteps)

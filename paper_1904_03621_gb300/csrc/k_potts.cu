@@ -246,12 +246,13 @@ __global__ void __launch_bounds__(kPottsSeedThreads) potts_seed_kernel(const Pot
 struct PottsSmem {
     int* Jq;                  // n*n
     int* hq;                  // n*q
-    int* Gt;                  // [walk][B*(Q-1)][threads]: exact G_k(v) of each walk
+    int* Gt;                  // [walk][B*Q][threads]: exact f_k(v) of each walk (fields of the inner digits)
     int* Ct;                  // [walk][m*Q][threads]: exact C_p(v) of each walk's middle digits
     int* E;                   // 2*cap
     unsigned long long* C;    // 2*cap
-    int* step;                // q^B: Gray step t changes table entry step[t] >> 1, upward if step[t] & 1
+    int* step;                // q^B: Gray step t moves digit k from v to v+1 (or back): (k Q + v) << 1 | up
     int* xin;                 // q^B: inner configuration sum_k d_k q^k after step t
+    int* mchg;                // q^m: the middle-digit change after block u: pm | a << 8 | a2 << 16
 };
 
 // integer packing hi * 2^16 + lo of two signed 16-bit increments
@@ -326,11 +327,11 @@ __device__ __forceinline__ int gray_digit32(unsigned u, int pos)
 // Gray steps t = L*R .. L*R + R - 1.  It evaluates its first configuration directly:
 //   E = Ebase + sum_k (f_k(d_k) - f_k(0)) - sum_{k<l<B} J_kl [d_k != d_l]
 // (Ebase has all inner digits 0, so every inner pair is equal there), then follows the
-// steps as the walk does: +-G_k(v) for the changed digit plus the pair-table difference.
-// G points at the walk's field table G_k(v) = f_k(v+1) - f_k(v), entry e at G[e * threads].
+// steps as the walk does: +-(f_k(v+1) - f_k(v)) for the changed digit plus the pair-table
+// difference.  F points at the walk's field table f_k(v), entry k Q + v at F[(k Q + v) * threads].
 template <int Q, int B>
 __device__ __forceinline__ void potts_warp_rescan(const PottsParams& p, const PottsSmem& s, unsigned* buf_count,
-                                                  unsigned ebase, const int* G, unsigned long long cb, int tau,
+                                                  unsigned ebase, const int* F, unsigned long long cb, int tau,
                                                   int tie_E, unsigned long long tie_C, int n, int lane)
 {
     constexpr int P = (int)potts_pow(Q, B);
@@ -348,15 +349,15 @@ __device__ __forceinline__ void potts_warp_rescan(const PottsParams& p, const Po
     unsigned e = ebase;
 #pragma unroll
     for (int k = 0; k < B; k++) {
-        for (int v = 0; v < d[k]; v++) e += (unsigned)G[(k * (Q - 1) + v) * kPottsThreads];
+        e += (unsigned)(F[(k * Q + d[k]) * kPottsThreads] - F[(k * Q) * kPottsThreads]);
 #pragma unroll
         for (int l = k + 1; l < B; l++)
             if (d[k] != d[l]) e -= (unsigned)s.Jq[k * n + l];
     }
     for (int t = t0; t < t1; t++) {
         if (t > t0) {
-            const int st = s.step[t];
-            const unsigned g = (unsigned)G[(st >> 1) * kPottsThreads];
+            const int st = s.step[t], kv = st >> 1;
+            const unsigned g = (unsigned)(F[(kv + 1) * kPottsThreads] - F[kv * kPottsThreads]);
             e += ((st & 1) ? g : 0u - g) + (unsigned)c_pdT[t];
         }
         const int ei = (int)e;
@@ -377,7 +378,7 @@ __global__ void __launch_bounds__(kPottsThreads, 2) potts_walk_kernel(const __gr
 {
     constexpr int B = potts_inner_digits(Q);
     constexpr int P = (int)potts_pow(Q, B);
-    constexpr int NG = B * (Q - 1);
+    constexpr int NF = B * Q;                 // per-walk field table entries f_k(v)
     constexpr int NW = kPottsWalks;
     static_assert(NW == 2, "two walks: the two 16-bit lanes of one register");
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -386,11 +387,12 @@ __global__ void __launch_bounds__(kPottsThreads, 2) potts_walk_kernel(const __gr
     s.C = reinterpret_cast<unsigned long long*>(smem_raw);
     s.E = reinterpret_cast<int*>(s.C + 2 * cap);
     s.Gt = s.E + 2 * cap;
-    s.Ct = s.Gt + NW * NG * kPottsThreads;
+    s.Ct = s.Gt + NW * NF * kPottsThreads;
     s.Jq = s.Ct + NW * kPottsMidTable * kPottsThreads;
     s.hq = s.Jq + n * n;
     s.step = s.hq + n * Q;
     s.xin = s.step + P;
+    s.mchg = s.xin + P;
 
     __shared__ unsigned s_buf_count;
     __shared__ int s_list_count, s_kE;
@@ -417,9 +419,16 @@ __global__ void __launch_bounds__(kPottsThreads, 2) potts_walk_kernel(const __gr
             const int k = potts_qval((unsigned long long)t, Q);
             const int a0 = potts_gray_digit((unsigned long long)(t - 1), Q, k);
             const int a1 = potts_gray_digit((unsigned long long)t, Q, k);
-            st = ((k * (Q - 1) + (a1 > a0 ? a0 : a1)) << 1) | (a1 > a0 ? 1 : 0);
+            st = ((k * Q + (a1 > a0 ? a0 : a1)) << 1) | (a1 > a0 ? 1 : 0);
         }
         s.step[t] = st;
+    }
+    // the middle-digit change after block u (u + 1 < q^m <= kPottsMaxBlocks): the digit pm = the
+    // q-adic valuation of u + 1 moves from a to a2, the same for every walk of the launch
+    for (int u = tid; u + 1 < (int)p.qpow[p.m] && u < kPottsMaxBlocks; u += blockDim.x) {
+        const int pm = qval32<Q>((unsigned)u + 1u);
+        const int a = gray_digit32<Q>((unsigned)u, pm), a2 = gray_digit32<Q>((unsigned)u + 1u, pm);
+        s.mchg[u] = pm | (a << 8) | (a2 << 16);
     }
     if (tid == 0) {
         s_buf_count = 0u;
@@ -486,7 +495,7 @@ __global__ void __launch_bounds__(kPottsThreads, 2) potts_walk_kernel(const __gr
                     if (d[i] == d[j]) e += (unsigned)s.Jq[i * n + j];
             }
             Ebase[w] = e;
-            // G_k(v) = f_k(v+1) - f_k(v), f_k(v) = h_k(v) + sum_{l >= B} J_kl [v == d_l]
+            // f_k(v) = h_k(v) + sum_{l >= B} J_kl [v == d_l] (fields of the inner digits from the rest)
             for (int k = 0; k < B; k++) {
                 int f[Q];
 #pragma unroll
@@ -497,7 +506,7 @@ __global__ void __launch_bounds__(kPottsThreads, 2) potts_walk_kernel(const __gr
                     for (int v = 0; v < Q; v++) f[v] += (d[l] == v) ? jv : 0;
                 }
 #pragma unroll
-                for (int v = 0; v < Q - 1; v++) Gt[(w * NG + k * (Q - 1) + v) * kPottsThreads] = f[v + 1] - f[v];
+                for (int v = 0; v < Q; v++) Gt[(w * NF + k * Q + v) * kPottsThreads] = f[v];
             }
             // C_p(v) = sum_{l != B+p} J_{B+p, l} [d_l == v] for the middle digits
             for (int pm = 0; pm < m; pm++) {
@@ -521,14 +530,16 @@ __global__ void __launch_bounds__(kPottsThreads, 2) potts_walk_kernel(const __gr
             unsigned G[B][Q - 1];
 #pragma unroll
             for (int k = 0; k < B; k++) {
-                int F0 = 0, F1 = 0;                     // cumulative F_k(v) of the two walks
+                // cumulative offsets F_k(v) = f_k(v) - f_k(0) of the two walks and their floors
+                const int b0 = Gt[(0 * NF + k * Q) * kPottsThreads], b1 = Gt[(1 * NF + k * Q) * kPottsThreads];
+                int h0 = 0, h1 = 0;                     // floor(F_k(v) / 2^16), F_k(0) = 0
 #pragma unroll
                 for (int v = 0; v < Q - 1; v++) {
-                    const int n0 = F0 + Gt[(0 * NG + k * (Q - 1) + v) * kPottsThreads];
-                    const int n1 = F1 + Gt[(1 * NG + k * (Q - 1) + v) * kPottsThreads];
-                    G[k][v] = pack2((n0 >> 16) - (F0 >> 16), (n1 >> 16) - (F1 >> 16));
-                    F0 = n0;
-                    F1 = n1;
+                    const int n0 = (int)((unsigned)Gt[(0 * NF + k * Q + v + 1) * kPottsThreads] - (unsigned)b0) >> 16;
+                    const int n1 = (int)((unsigned)Gt[(1 * NF + k * Q + v + 1) * kPottsThreads] - (unsigned)b1) >> 16;
+                    G[k][v] = pack2(n0 - h0, n1 - h1);
+                    h0 = n0;
+                    h1 = n1;
                 }
             }
             unsigned X = pack_e16((int)Ebase[0], (int)Ebase[1]);
@@ -549,7 +560,7 @@ __global__ void __launch_bounds__(kPottsThreads, 2) potts_walk_kernel(const __gr
                         todo &= todo - 1u;
                         const unsigned eb = __shfl_sync(0xffffffffu, Ebase[w], src);
                         const unsigned long long cw = __shfl_sync(0xffffffffu, c0[w], src);
-                        const int* Gs = s.Gt + (tid - lane + src) + w * NG * kPottsThreads;
+                        const int* Gs = s.Gt + (tid - lane + src) + w * NF * kPottsThreads;
                         potts_warp_rescan<Q, B>(p, s, &s_buf_count, eb, Gs, cw + midc, tau_scr, tie_E, tie_C, n,
                                                 lane);
                     }
@@ -600,8 +611,8 @@ __global__ void __launch_bounds__(kPottsThreads, 2) potts_walk_kernel(const __gr
 
             // ---- change one middle digit: pm = q-adic valuation of u + 1, a -> a2 (both walks)
             if (u + 1 < nblocks) {
-                const int pm = qval32<Q>((unsigned)u + 1u);
-                const int a = gray_digit32<Q>((unsigned)u, pm), a2 = gray_digit32<Q>((unsigned)u + 1u, pm);
+                const int mc = s.mchg[u];
+                const int pm = mc & 0xff, a = (mc >> 8) & 0xff, a2 = mc >> 16;
                 const int sp = B + pm;
 #pragma unroll
                 for (int w = 0; w < NW; w++) {
@@ -610,12 +621,10 @@ __global__ void __launch_bounds__(kPottsThreads, 2) potts_walk_kernel(const __gr
                                 (unsigned)(s.hq[sp * Q + a2] - s.hq[sp * Q + a]);
                     for (int k = 0; k < B; k++) {
                         const int jv = s.Jq[k * n + sp];
-                        int* g = Gt + (w * NG + k * (Q - 1)) * kPottsThreads;
+                        int* g = Gt + (w * NF + k * Q) * kPottsThreads;
                         // f_k(a) -= J, f_k(a2) += J
-                        if (a >= 1) g[(a - 1) * kPottsThreads] -= jv;
-                        if (a <= Q - 2) g[a * kPottsThreads] += jv;
-                        if (a2 >= 1) g[(a2 - 1) * kPottsThreads] += jv;
-                        if (a2 <= Q - 2) g[a2 * kPottsThreads] -= jv;
+                        g[a * kPottsThreads] -= jv;
+                        g[a2 * kPottsThreads] += jv;
                     }
                     for (int p2 = 0; p2 < m; p2++) {
                         if (p2 == pm) continue;
@@ -638,9 +647,9 @@ __global__ void __launch_bounds__(kPottsThreads, 2) potts_walk_kernel(const __gr
 size_t potts_walk_smem(int q, int n, int list_cap)
 {
     const int B = potts_inner_digits(q);
-    return (size_t)2 * list_cap * 12 + (size_t)kPottsWalks * B * (q - 1) * kPottsThreads * 4 +
+    return (size_t)2 * list_cap * 12 + (size_t)kPottsWalks * B * q * kPottsThreads * 4 +
            (size_t)kPottsWalks * kPottsMidTable * kPottsThreads * 4 + (size_t)n * n * 4 + (size_t)n * q * 4 +
-           (size_t)potts_pow(q, B) * 8;
+           (size_t)potts_pow(q, B) * 8 + (size_t)kPottsMaxBlocks * 4;
 }
 
 template <int Q>
