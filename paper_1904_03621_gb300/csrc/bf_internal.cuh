@@ -282,7 +282,8 @@ constexpr int kBMaxN = 32;                       // largest n of the batched wal
 constexpr int kBMaxS = 64;
 
 struct BInst {                                   // per-instance constants (device)
-    int n, q, W, m, nh, status;
+    int n, q, W, m, nh, status;                  // n: spins the walker enumerates
+    int n_full, z2;                              // the instance's spins; 1: zero fields, half space walked
     unsigned long long units;                    // work units (128 tasks each)
     double delta, emax;
     int Jq[kBMaxN * kBMaxN];

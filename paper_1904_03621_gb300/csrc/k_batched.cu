@@ -127,6 +127,7 @@ __global__ void __launch_bounds__(kBPrepThreads, 4) bprep_kernel(const BatchPara
     __shared__ int hq[kBMaxN];
     __shared__ int Tw[kBWalkSteps];                  // the walker's inner pair energies
     __shared__ int s_lists[kBPrepThreads / 32 * kBMaxS], s_kth;   // kth_lowest's warp lists
+    __shared__ int s_z2;
     __shared__ int s_q, s_status, s_tau, s_dE[kBPrepThreads / 32], s_F[kBMaxN];
     __shared__ unsigned long long s_dC[kBPrepThreads / 32];
     __shared__ double s_emax;
@@ -137,6 +138,8 @@ __global__ void __launch_bounds__(kBPrepThreads, 4) bprep_kernel(const BatchPara
     if (n < kBMinN || n > p.n_max || n > kBMaxN || (1ll << n) < p.S) {
         if (tid == 0) {
             I->n = n;
+            I->n_full = n;
+            I->z2 = 0;
             I->status = kErrArg;
             I->units = 0;
             atomicOr(&p.hdr->status, kErrArg);
@@ -206,6 +209,14 @@ __global__ void __launch_bounds__(kBPrepThreads, 4) bprep_kernel(const BatchPara
         if (p.dtype != 0) I->Rh[lane] = __double2ll_rn(ldexp(t - r, kBResBits));
     }
     const double delta = ldexp(block_sum(part, red), -q);
+    // zero fields: E(c) = E(~c), so the walker searches the half space with the top spin at -1
+    // (an instance of n - 1 spins with fields h'_i = -J_{i,n-1}) and the final selection adds
+    // each record's mirror.  The bound of the first threshold below stays valid: the distinct
+    // configurations it ranks map to distinct configurations of the half space (c or ~c).
+    if (warp == 0) {
+        const bool hz = __all_sync(0xffffffffu, lane >= n || hd[lane] == 0.0);
+        if (lane == 0) s_z2 = (hz && n - 1 >= kBMinN) ? 1 : 0;
+    }
     static_assert(kBWalkBits <= kBMinN, "the walker's inner spins exist in every instance");
     // inner pair energies T[g] = sum_{i<k} J_ik s_i s_k over the walker's inner spins: the pairs
     // below the top inner spin by the definition, then T = t -+ f_top for the top spin at -1 / +1
@@ -335,9 +346,11 @@ __global__ void __launch_bounds__(kBPrepThreads, 4) bprep_kernel(const BatchPara
         if (tid == 0 && t < s_tau) s_tau = t;
     }
     __syncthreads();
-    // outputs
-    for (int idx = tid; idx < n * n; idx += blockDim.x) I->Jq[idx] = Jq[idx];
-    for (int i = tid; i < kBMaxN; i += blockDim.x) I->hq[i] = i < n ? hq[i] : 0;
+    // outputs: the walked instance (n_w spins; the half space for zero fields)
+    const int z2 = s_z2, nw = n - z2;
+    for (int idx = tid; idx < nw * nw; idx += blockDim.x) I->Jq[idx] = Jq[(idx / nw) * n + idx % nw];
+    for (int i = tid; i < kBMaxN; i += blockDim.x)
+        I->hq[i] = i < nw ? (z2 ? -Jq[i * n + (n - 1)] : hq[i]) : 0;
     for (int g = tid; g < kBWalkSteps; g += blockDim.x) {
         I->T[g] = Tw[g];
         unsigned v = 0;
@@ -350,7 +363,7 @@ __global__ void __launch_bounds__(kBPrepThreads, 4) bprep_kernel(const BatchPara
     for (int idx = tid; idx < kBMaxN * 16; idx += blockDim.x) {
         int j = idx / 16, k = idx % 16;
         int row = k < kBWalkBits + kKeep ? k : -1;
-        I->col[j][k] = (j < n && row >= 0 && row < n) ? Jq[row * n + j] : 0;
+        I->col[j][k] = (j < nw && row >= 0 && row < nw) ? Jq[row * n + j] : 0;
     }
     if (tid == 0) {
         int status = s_status;
@@ -361,10 +374,12 @@ __global__ void __launch_bounds__(kBPrepThreads, 4) bprep_kernel(const BatchPara
             if (w > (double)(1 << 28)) { w = (double)(1 << 28); status |= kErrRange; }
             W = (int)w;
         }
-        int m = n - kBWalkBits - kBUnitWalkBits;   // 2^10 tasks per unit
+        int m = nw - kBWalkBits - kBUnitWalkBits;   // 2^10 tasks per unit
         m = m < 0 ? 0 : (m > p.m_cap ? p.m_cap : m);
-        const int nh = n - kBWalkBits - m;
-        I->n = n;
+        const int nh = nw - kBWalkBits - m;
+        I->n = nw;
+        I->n_full = n;
+        I->z2 = z2;
         I->q = q;
         I->W = W;
         I->m = m;
@@ -931,8 +946,33 @@ __global__ void __launch_bounds__(kBFinalThreads) bfinal_kernel(const BatchParam
     }
     __syncthreads();
     const int keep = s_keep;
-    const int n = I->n;
+    const int n = I->n_full;
+    // Zero fields (I->z2): the records are the half space's lowest (top spin at -1).  With their
+    // mirrors c ^ (2^n - 1), of the same energy, they contain the S lowest of the whole space: a
+    // mirror's original precedes it in (E, c) order.  Within one energy level the half-space
+    // records (c < 2^(n-1)) come first in increasing c, then the mirrors in the reverse order of
+    // their originals.  One thread writes the S outputs from the sorted list (S <= 64).
+    const unsigned long long mirror = (n >= 64 ? ~0ull : (1ull << n) - 1ull);
+    auto emit_mirrored = [&](auto key_at, auto write) {
+        int out = 0, i = 0;
+        while (out < S && i < keep) {
+            int j = i + 1;
+            while (j < keep && key_at(j) == key_at(i)) j++;
+            for (int t = i; t < j && out < S; t++) write(out++, t, 0ull);
+            for (int t = j - 1; t >= i && out < S; t--) write(out++, t, mirror);
+            i = j;
+        }
+        for (; out < S; out++) write(out, -1, 0ull);
+    };
     if (p.dtype == 0) {
+        if (I->z2) {
+            if (threadIdx.x == 0)
+                emit_mirrored([&](int t) { return E[t]; }, [&](int k, int t, unsigned long long x) {
+                    static_cast<long long*>(p.energies)[(size_t)b * S + k] = t >= 0 ? (long long)(E[t] >> I->q) : LLONG_MAX;
+                    p.states[(size_t)b * S + k] = t >= 0 ? C[t] ^ x : kEmptyC;
+                });
+            return;
+        }
         for (int k = threadIdx.x; k < S; k += blockDim.x) {
             static_cast<long long*>(p.energies)[(size_t)b * S + k] = k < keep ? (long long)(E[k] >> I->q) : LLONG_MAX;
             p.states[(size_t)b * S + k] = C[k];
@@ -973,6 +1013,14 @@ __global__ void __launch_bounds__(kBFinalThreads) bfinal_kernel(const BatchParam
     for (int i = threadIdx.x; i < lenk; i += blockDim.x)
         if (i >= keep) C[i] = kEmptyC;
     block_sort(E64, C, lenk);
+    if (I->z2) {
+        if (threadIdx.x == 0)
+            emit_mirrored([&](int t) { return E64[t]; }, [&](int k, int t, unsigned long long x) {
+                static_cast<double*>(p.energies)[(size_t)b * S + k] = t >= 0 ? E64[t] : DBL_MAX;
+                p.states[(size_t)b * S + k] = t >= 0 ? C[t] ^ x : kEmptyC;
+            });
+        return;
+    }
     for (int k = threadIdx.x; k < S; k += blockDim.x) {
         static_cast<double*>(p.energies)[(size_t)b * S + k] = E64[k];
         p.states[(size_t)b * S + k] = C[k];

@@ -64,6 +64,32 @@ def test_batched_mixed_float(bf, o, S):
     check_all(o, insts, en.cpu().numpy(), bf.states_u64(st).reshape(en.shape), S)
 
 
+@pytest.mark.parametrize("S", [5, 33])
+def test_batched_scales_and_windows(bf, o, S):
+    """One batch whose instances differ in scale by 18 orders of magnitude (the per-instance
+    fixed-point exponent q from about -30 to +60), plus integer-valued float instances
+    (residual 0, no window) and near-integer ones (tiny residuals, a window of a few units):
+    the quantisation, the residual words and the final re-evaluation of every instance must
+    reproduce the oracle.  n from 10 (the exact sample) to 22."""
+    rng = np.random.default_rng(400 + S)
+    insts = []
+    for i, scale in enumerate([1e-9, 1e-3, 1.0, 1e3, 1e9] * 3):
+        n = int(rng.integers(10, 23))
+        J, h = instances.dense_gaussian(n, 500 + i, h_std=0.7)
+        insts.append((J * scale, h * scale))
+    for i in range(6):
+        n = int(rng.integers(10, 23))
+        J, h = instances.dense_pm1(n, 600 + i)
+        J, h = J.astype(np.float64), h.astype(np.float64)
+        if i % 2:   # near-integer couplings: residuals of about 1e-7
+            N = np.triu(rng.normal(0.0, 1e-7, J.shape), 1)
+            J = J + N + N.T
+        insts.append((J, h))
+    args = bf.pack_batch(insts)
+    en, st = bf.low_spectrum_batched(*args[:5], S, n_max=args[5], task_log2=21)
+    check_all(o, insts, en.cpu().numpy(), bf.states_u64(st).reshape(en.shape), S)
+
+
 def test_batched_int(bf, o):
     rng = np.random.default_rng(7)
     insts = [instances.dense_pm1(int(rng.integers(10, 22)), 50 + i) for i in range(24)]
