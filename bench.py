@@ -251,6 +251,10 @@ def batched_section(api, torch, dev, steps, warmup):
     S = 10
     B = len(insts)
     configs = float(sum(2.0 ** t[0].shape[0] for t in insts))
+    # configurations the walker enumerates: instances with zero fields (n >= 11) walk half
+    # their space (Z2 symmetry, the mirrors are added by the final selection)
+    walked = float(sum(2.0 ** (t[0].shape[0] - (1 if t[0].shape[0] >= 11 and not np.any(t[1]) else 0))
+                       for t in insts))
     tuned = api.autotune_batched(J, Jo, h, ho, n, S, n_max=n_max)      # cached for the default calls below
     ws = torch.empty(api.batched_workspace_size(B, n_max, S, torch.float64), dtype=torch.uint8, device=dev)
     en = torch.empty(B, S, dtype=torch.float64, device=dev)
@@ -291,6 +295,9 @@ def batched_section(api, torch, dev, steps, warmup):
     out = {"workload": "batched_4096: 2048 dense (n~U{16..28}, J~N(0,1), h~N(0,0.5^2)) + 2048 Chimera "
                        "(n~U{16..28}, J=+-1, h=0), S=10, one graph-replayed launch sequence",
            "instances_per_s": B / (ms * 1e-3), "configs_per_s": configs / (ms * 1e-3), "ms_per_step": ms,
+           "walked_configs_per_s": walked / (ms * 1e-3),
+           "walked_note": "configs_per_s counts all 2^n configurations each instance is solved over; the 2048 "
+                          "zero-field (Chimera) instances enumerate half of them (Z2 symmetry)",
            "autotuned": tuned,
            "steps": steps, "plain_instances_per_s": plain_ips,
            "plain_sample": f"{len(sample)} instances, one bf_low_spectrum call each",
@@ -549,8 +556,10 @@ def batched_only(args):
             times.append(ev0.elapsed_time(ev1) / 1e3)
     t = float(np.median(times))
     configs = float(sum(2.0 ** J.shape[0] for J, _, _ in insts))
+    walked = float(sum(2.0 ** (J.shape[0] - (1 if J.shape[0] >= 11 and not np.any(h) else 0)) for J, h, _ in insts))
     print(json.dumps({"metric": "batched instances/s (exact top-S)", "value": len(insts) / t, "unit": "instances/s",
-                      "configs_per_s": configs / t, "ms_per_step": t * 1e3, "steps": args.steps,
+                      "configs_per_s": configs / t, "walked_configs_per_s": walked / t, "ms_per_step": t * 1e3,
+                      "steps": args.steps,
                       "warmup": args.warmup, "autotuned": tuned, "config": {"workload": "batched_4096", "S": S}}),
           flush=True)
     return 0
@@ -835,8 +844,9 @@ def main():
     }
     if not args.no_batched:
         bsec = batched_section(api, torch, dev, max(args.steps, 3), max(args.warmup, 3))
-        # the whole batched call (preparation, walk, final selection) against the walk's issue peak
-        bsec["issue_roofline_frac"] = bsec["configs_per_s"] * ALU_OPS_PER_CONFIG / peak_ops
+        # the whole batched call (preparation, walk, final selection) against the walk's issue peak,
+        # counting the configurations it enumerates
+        bsec["issue_roofline_frac"] = bsec["walked_configs_per_s"] * ALU_OPS_PER_CONFIG / peak_ops
         line["batched"] = bsec
         line["configs"] = config_checks(api, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
