@@ -22,8 +22,11 @@
  *     is therefore unique.
  *   - Integer instances (BF_I32) are exact.  Float instances (BF_F32, BF_F64)
  *     are screened in exact fixed point with a rigorous quantisation bound and
- *     every surviving candidate is re-evaluated in FP64; returned energies are
- *     FP64 values of Eq. (1).
+ *     every surviving candidate is re-evaluated from the input values: an FP64
+ *     sum of Eq. (1), or (spaces of at most 2^20 configurations, the batched
+ *     search) the quantised energy plus the rounding residuals summed exactly in
+ *     64-bit fixed point and rounded once to FP64.  Returned energies are FP64
+ *     values of Eq. (1) and the final order is taken on them.
  *
  * Memory and streams: every pointer argument named "device" is device memory
  * owned by the caller and must stay valid until the work queued on `stream`
@@ -349,7 +352,7 @@ bf_status bf_low_spectrum_qubo(const void* a, const void* b, int n, int S, bf_dt
  *   J          device, n*n values of `dtype`, row-major; strict upper triangle read
  *   h          device, n*q values of `dtype`, row-major: h[i*q + v] = h_i(v)
  *   energies   device out, S values: int64 for BF_I32 (exact), double otherwise
- *              (FP64 re-evaluation of every candidate, as for bf_low_spectrum)
+ *              (every candidate re-evaluated in FP64, as for bf_low_spectrum)
  *   states     device out, S configuration integers
  *   workspace  device, >= bf_potts_workspace_size(...) bytes, 256-byte aligned
  * Options: task/grid/spill/profile fields as for bf_low_spectrum; fixed_bits
