@@ -363,6 +363,14 @@ bf_status low_spectrum_impl(const void* J, const void* h, int n, int S, bf_dtype
     pp.range_flag = range_flag;
     pp.prep = prep;
     pp.hdr = hdr;
+    // Zero-field instances walk the half space with spin n-1 at -1 (E(c) = E(~c)); the device
+    // decides from h.  Allowed for the Gray walk over the whole space whose first threshold is a
+    // single Hamming ball (its distinct configurations map to distinct half-space ones; a sample
+    // or a union of balls could hold both c and ~c), when spin n-1 is a task bit (the walk
+    // takes the lower half of the task range), and not while the autotuner times a part of the
+    // task queue.
+    pp.z2_ok = (pl.variant == BF_VARIANT_GRAY && pl.free_bits == n && pl.nh >= 1 && pl.descent_blocks &&
+                bf::ball_size(pl.free_bits) >= S && !tune_configs) ? 1 : 0;
     cudaError_t e = bf::launch_prep(pp, stream);
     if (e != cudaSuccess) return cuda_fail(e, "prep kernel");
 
@@ -483,7 +491,7 @@ bf_status low_spectrum_impl(const void* J, const void* h, int n, int S, bf_dtype
     const int* FE = in_a ? AE : BE;
     const unsigned long long* FC = in_a ? AC : BC;
     e = bf::launch_finalize(FE, FC, L.list_cap, S, n, dtype, 0, J, h, reinterpret_cast<double*>(ws + L.rescore),
-                            energies, out_states, hdr, stream, qd);
+                            energies, out_states, hdr, stream, qd, &prep->L.z2);
     if (e != cudaSuccess) return cuda_fail(e, "finalize");
     return BF_OK;
 }

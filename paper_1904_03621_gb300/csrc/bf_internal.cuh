@@ -71,6 +71,7 @@ struct PrepLaunch {
     int tau0;             // seed threshold (INT32 max if none)
     double delta;         // quantisation residual bound (energy units)
     double emax;          // sum |J| + sum |h| (energy units)
+    int z2;               // 1: zero fields, the walk covers the half space with spin n-1 at -1
     unsigned dT16[kGrayMaxInnerSteps];   // packed 16-bit pair-energy increments of the inner walk
 };
 
@@ -178,6 +179,7 @@ struct PrepParams {
     unsigned long long hiconst;
     int emq_log2;                   // |E_q| and |local fields| < 2^emq_log2
     int inner_bits;                 // inner spins of the Gray walk the tables are built for
+    int z2_ok;                      // the plan allows the half-space walk of zero-field instances
     const unsigned* range_flag;     // optional: nonzero *range_flag marks the instance out of range
     Prep* prep;
     WsHeader* hdr;
@@ -378,10 +380,12 @@ cudaError_t launch_small(const SmallParams& p, cudaStream_t s);
 // Final selection: integer instances write E_q >> q; float instances
 // re-evaluate Eq. (1) in FP64 from the caller's J, h and reselect.
 // qp != nullptr: the scale exponent is read on the device from *qp instead of q.
+// z2p != nullptr and *z2p: the list holds the half space with spin n-1 at -1 of a zero-field
+// instance; the S outputs include the mirrors c ^ (2^n - 1).
 cudaError_t launch_finalize(const int* E, const unsigned long long* C, int cap, int S, int n, int dtype,
                             int q, const void* J, const void* h, double* rescore,
                             void* energies, unsigned long long* states, WsHeader* hdr, cudaStream_t s,
-                            const int* qp = nullptr);
+                            const int* qp = nullptr, const int* z2p = nullptr);
 // Seed: `blocks` lists of the lowest sampled records (sample configurations in total).
 cudaError_t launch_seed(const Prep* prep, int n, int free_bits, unsigned long long hiconst,
                         unsigned long long sample, int per_block, int blocks, int cap, int* outE,

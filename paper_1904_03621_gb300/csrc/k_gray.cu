@@ -202,6 +202,9 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
     __syncthreads();
 
     const int S = p.S, W = prep->L.W, m = p.m;
+    // zero-field instances (prep->L.z2): the lower half of the task range, whose top task bit
+    // (spin n - 1) is 0; the final selection adds the mirrors
+    const unsigned long long ntasks = p.ntasks >> prep->L.z2;
     const int walk_shift = IB + m;       // task index sits above inner + middle spins
     const unsigned nblocks = 1u << m;
     const unsigned seg_mask = (1u << p.seg_log2) - 1u;
@@ -230,7 +233,7 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
         __syncthreads();
         const unsigned long long base = s_batch;
         __syncthreads();
-        if (base >= p.ntasks) break;
+        if (base >= ntasks) break;
 
         // ---- per-walk state at the start of the task (middle and inner spins all -1)
         int E0[kWalks], G[kWalks][IB], Fm[kWalks][kKeep];
@@ -320,7 +323,7 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
 #pragma unroll
             for (int w = 0; w < kWalks; w++) {
                 // an inactive walk (task >= ntasks) keeps a valid configuration; its hits are ignored
-                active[w] = base + (unsigned long long)(xt + w) < p.ntasks;
+                active[w] = base + (unsigned long long)(xt + w) < ntasks;
                 unsigned e = ER + Et;
                 unsigned g[IB], fm[kKeep];
 #pragma unroll
@@ -354,7 +357,7 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
 #pragma unroll
             for (int w = 0; w < kWalks; w++) {
                 unsigned long long task = base + (unsigned long long)(tid * kWalks + w);
-                active[w] = task < p.ntasks;
+                active[w] = task < ntasks;
                 if (!active[w]) task = 0;   // a valid walk whose hits are ignored
                 cfg0[w] = p.hiconst | (task << walk_shift);
             }

@@ -173,6 +173,11 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(const PrepParams p)
             if (w > (double)(1 << 28)) { w = (double)(1 << 28); status |= kErrRange; }
             W = (int)w;
         }
+        // zero fields: E(c) = E(~c), so the walk covers the configurations with spin n-1 at -1
+        // (the lower half of the task range) and the final selection adds the mirrors
+        int hz = p.z2_ok;
+        for (int i = 0; i < n && hz; i++) hz = hd[i] == 0.0;
+        out->L.z2 = hz;
         out->L.status = status;
         out->L.q = q;
         out->L.W = W;

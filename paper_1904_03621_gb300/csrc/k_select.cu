@@ -111,11 +111,43 @@ __global__ void __launch_bounds__(kMergeThreads) absorb_kernel(int* LE, unsigned
 
 // ---- final selection -------------------------------------------------------
 
+// Zero-field searches walk the half space with spin n-1 at -1: the sorted list holds its lowest
+// records, and with their mirrors c ^ (2^n - 1), of the same energy, they contain the S lowest of
+// the whole space (a mirror's original has the smaller c, so it comes first in (E, c) order).
+// Within one energy the half-space records come first in increasing c, then the mirrors in the
+// reverse order.  One thread writes the S outputs; key_at(t) is the t-th sorted key, and real
+// records end at the first empty one.
+template <typename KeyAt, typename Empty, typename Write>
+__device__ void emit_with_mirrors(int len, int S, int n, KeyAt key_at, Empty empty, Write write)
+{
+    const unsigned long long mirror = n >= 64 ? ~0ull : (1ull << n) - 1ull;
+    int keep = 0;
+    while (keep < len && !empty(keep)) keep++;
+    int out = 0, i = 0;
+    while (out < S && i < keep) {
+        int j = i + 1;
+        while (j < keep && key_at(j) == key_at(i)) j++;
+        for (int t = i; t < j && out < S; t++) write(out++, t, 0ull);
+        for (int t = j - 1; t >= i && out < S; t--) write(out++, t, mirror);
+        i = j;
+    }
+    for (; out < S; out++) write(out, -1, 0ull);
+}
+
 __global__ void __launch_bounds__(256) finalize_int_kernel(const int* E, const unsigned long long* C, int S, int q,
-                                                           const int* qp, long long* energies,
-                                                           unsigned long long* states)
+                                                           const int* qp, const int* z2p, int n, int len,
+                                                           long long* energies, unsigned long long* states)
 {
     if (qp) q = *qp;
+    if (z2p && *z2p) {
+        if (blockIdx.x == 0 && threadIdx.x == 0)
+            emit_with_mirrors(len, S, n, [&](int t) { return E[t]; }, [&](int t) { return E[t] == kEmptyE; },
+                              [&](int k, int t, unsigned long long x) {
+                                  energies[k] = t >= 0 ? (long long)(E[t] >> q) : LLONG_MAX;
+                                  states[k] = t >= 0 ? C[t] ^ x : kEmptyC;
+                              });
+        return;
+    }
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < S; k += gridDim.x * blockDim.x) {
         energies[k] = (long long)(E[k] >> q);   // E_q = E * 2^q exactly for integer instances
         states[k] = C[k];
@@ -156,8 +188,8 @@ __global__ void __launch_bounds__(256) rescore_kernel(const int* E, const unsign
 }
 
 __global__ void __launch_bounds__(kMergeThreads) finalize_float_kernel(const unsigned long long* C, const double* E64,
-                                                                       int cap, int S, double* energies,
-                                                                       unsigned long long* states)
+                                                                       int cap, int S, const int* z2p, int n,
+                                                                       double* energies, unsigned long long* states)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long* cfg = reinterpret_cast<unsigned long long*>(smem);
@@ -167,6 +199,15 @@ __global__ void __launch_bounds__(kMergeThreads) finalize_float_kernel(const uns
         cfg[i] = C[i];
     }
     block_sort(key, cfg, cap);
+    if (z2p && *z2p) {
+        if (threadIdx.x == 0)
+            emit_with_mirrors(cap, S, n, [&](int t) { return key[t]; }, [&](int t) { return cfg[t] == kEmptyC; },
+                              [&](int k, int t, unsigned long long x) {
+                                  energies[k] = t >= 0 ? key[t] : DBL_MAX;
+                                  states[k] = t >= 0 ? cfg[t] ^ x : kEmptyC;
+                              });
+        return;
+    }
     for (int k = threadIdx.x; k < S; k += blockDim.x) {
         energies[k] = key[k];
         states[k] = cfg[k];
@@ -201,11 +242,13 @@ cudaError_t launch_absorb_spill(int* E, unsigned long long* C, int nlists, int c
 
 cudaError_t launch_finalize(const int* E, const unsigned long long* C, int cap, int S, int n, int dtype, int q,
                             const void* J, const void* h, double* rescore, void* energies,
-                            unsigned long long* states, WsHeader* hdr, cudaStream_t s, const int* qp)
+                            unsigned long long* states, WsHeader* hdr, cudaStream_t s, const int* qp,
+                            const int* z2p)
 {
     (void)hdr;
     if (dtype == 0) {
-        finalize_int_kernel<<<(S + 255) / 256, 256, 0, s>>>(E, C, S, q, qp, static_cast<long long*>(energies), states);
+        finalize_int_kernel<<<(S + 255) / 256, 256, 0, s>>>(E, C, S, q, qp, z2p, n, cap,
+                                                            static_cast<long long*>(energies), states);
         count_launches(1);
         return cudaGetLastError();
     }
@@ -216,7 +259,8 @@ cudaError_t launch_finalize(const int* E, const unsigned long long* C, int cap, 
     size_t smem = (size_t)cap * 16;
     e = ensure_smem(reinterpret_cast<const void*>(finalize_float_kernel), (size_t)(smem));
     if (e != cudaSuccess) return e;
-    finalize_float_kernel<<<1, kMergeThreads, smem, s>>>(C, rescore, cap, S, static_cast<double*>(energies), states);
+    finalize_float_kernel<<<1, kMergeThreads, smem, s>>>(C, rescore, cap, S, z2p, n, static_cast<double*>(energies),
+                                                         states);
     count_launches(1);
     return cudaGetLastError();
 }

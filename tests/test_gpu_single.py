@@ -147,6 +147,39 @@ def test_plain_n20(bf, o):
     check(bf, o, J, h, 10)
 
 
+# ---- zero fields: the walk covers the half space with spin n-1 at -1 (Z2 symmetry) -------
+# S up to the Hamming-ball size 1 + n + n(n-1)/2 takes the half-space walk; larger S, fixed
+# top bits and the tensor-core variant walk the whole space.  Both must equal the oracle.
+@pytest.mark.parametrize("n,S,seed", [(21, 1, 0), (22, 100, 1), (24, 301, 2), (26, 352, 3), (22, 300, 4)])
+def test_zero_field_int(bf, o, n, S, seed):
+    J, h = rand_pm1(n, 900 + seed)
+    assert not np.any(h)
+    check(bf, o, J, h, S)
+
+
+@pytest.mark.parametrize("n,S,seed,dtype", [(21, 10, 0, np.float64), (23, 253, 1, np.float64),
+                                            (25, 100, 2, np.float32)])
+def test_zero_field_float(bf, o, n, S, seed, dtype):
+    J, h = rand_float(n, 950 + seed, dtype=dtype)
+    check(bf, o, J, np.zeros_like(h), S)
+
+
+def test_zero_field_ferromagnet_mirrors(bf, o):
+    """J = -1, h = 0 at n = 24: the ground states c = 0 and c = 2^24 - 1 are each other's
+    mirror, and every level pairs c with ~c."""
+    for dt in (np.int32, np.float64):
+        J, h = instances.ferromagnet(24, dtype=dt)
+        en, st = check(bf, o, J, h, 60)
+        assert st[0] == 0 and st[1] == (1 << 24) - 1
+
+
+def test_zero_field_whole_space_variants(bf, o):
+    J, h = rand_pm1(26, 990)
+    check(bf, o, J, h, 50, fixed_bits=3, fixed_value=5)
+    Jf, hf = rand_float(24, 991)
+    check(bf, o, Jf, np.zeros_like(hf), 50, variant=2)
+
+
 def test_ferromagnet(bf, o):
     for dt in (np.int32, np.float64):
         J, h = instances.ferromagnet(20, dtype=dt)
