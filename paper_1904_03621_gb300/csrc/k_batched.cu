@@ -5,21 +5,27 @@
 // (exact fixed point, Gray walk with the two-lane 16-bit pre-filter, exact
 // rescans), with these changes so that the whole sequence needs no host
 // synchronisation and can be captured in a CUDA graph:
-//   - the per-instance inner increments live in a shared-memory slot of the
-//     warp processing the instance (loaded with 128-bit loads, LSU pipe)
-//     instead of kernel parameters;
+//   - the per-instance inner increments live in shared memory, loaded once per
+//     work unit and read with 128-bit loads (LSU pipe) instead of kernel
+//     parameters;
 //   - a work unit is one block: 256 threads x 4 walks = 1024 tasks of
 //     2^(9+m) configurations; blocks pop units from a queue of waves (unit w
 //     of every instance, instances by decreasing n), and a barrier after every
 //     unrolled block keeps the block's warps on the same stretch of code
-//     (independent warps stalled on instruction fetch);
-//   - hits are collected warp-cooperatively: a flagged walk is rescanned by
-//     all 32 lanes (8 configurations each) into a bounded per-warp buffer that
-//     is merged (warp bitonic sort, keep rule) before it can overflow, so no
-//     spill area is needed;
+//     (independent warps stalled on instruction fetch); warp 0 evaluates the
+//     unit's common start once and every thread reaches its walks by a few
+//     flips;
+//   - each walk keeps one running 16-bit minimum per eighth of the block; hits
+//     are collected warp-cooperatively: the flagged eighths of a walk are
+//     rescanned by all 32 lanes (2 configurations each) into a bounded per-warp
+//     buffer that is merged (warp bitonic sort, keep rule) before it can
+//     overflow, so no spill area is needed;
 //   - each unit appends its surviving records to the instance's pool and
 //     lowers the instance threshold with atomicMin; a final kernel reselects
-//     each instance's S lowest (FP64 re-evaluation for float instances).
+//     each instance's S lowest (float instances: re-evaluated as the quantised
+//     energy plus the rounding residuals in 64-bit fixed point);
+//   - zero-field instances (h = 0) walk the half space with the top spin at -1
+//     (Z2 symmetry); the final kernel adds the mirrors.
 #include <cfloat>
 #include <climits>
 #include <utility>
