@@ -485,6 +485,16 @@ __global__ void __launch_bounds__(kGrayThreads, 2) gray_kernel(const __grid_cons
                         for (int r = 1; r < kKeep; r++) f = (jrel == r) ? Fm[w][r] : f;
                         F[w] = f;
                     }
+                } else if (active[0] && active[1] && active[2] && active[3]) {
+                    // the four walks differ only in the task spins a = walk_shift (walks 1, 3 at
+                    // +1) and a + 1 (walks 2, 3): one field by the definition, the others from it
+                    const int f0 = field_at(s, n, j, cfg0[0] | cmid);
+                    const int* Jj = s.Jq + j * n;
+                    const unsigned da = (unsigned)Jj[walk_shift] << 1, db = (unsigned)Jj[walk_shift + 1] << 1;
+                    F[0] = f0;
+                    F[1] = (int)((unsigned)f0 + da);
+                    F[2] = (int)((unsigned)f0 + db);
+                    F[3] = (int)((unsigned)f0 + da + db);
                 } else {
 #pragma unroll
                     for (int w = 0; w < kWalks; w++) F[w] = field_at(s, n, j, cfg0[w] | cmid);
