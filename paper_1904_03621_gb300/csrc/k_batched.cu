@@ -822,6 +822,17 @@ __global__ void __launch_bounds__(kBThreads, 2) bwalk_kernel(const BatchParams p
                         for (int r = 1; r < kKeep; r++) f = (jrel == r) ? Fm[w][r] : f;
                         F[w] = f;
                     }
+                } else if (active_mask == 0xfu) {
+                    // the four walks differ only in the walk spins sa (walks 1, 3 at +1) and sb
+                    // (walks 2, 3): one field by the definition, the others from it
+                    const unsigned long long c = cfg0[0] | cmid;
+                    int f = hq[j];
+                    for (int i = 0; i < n; i++) f += ((c >> i) & 1ull) ? Jq[j * n + i] : -Jq[j * n + i];
+                    const unsigned da = (unsigned)Jq[j * n + sa] << 1, db = (unsigned)Jq[j * n + sb] << 1;
+                    F[0] = f;
+                    F[1] = (int)((unsigned)f + da);
+                    F[2] = (int)((unsigned)f + db);
+                    F[3] = (int)((unsigned)f + da + db);
                 } else {
 #pragma unroll
                     for (int w = 0; w < kWalks; w++) {
