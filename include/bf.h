@@ -147,6 +147,11 @@ size_t bf_workspace_size(int n, int S, bf_dtype dtype, const bf_options* opt);
  * and replayed with new values in J and h (same n, S, dtype and options).
  * Instances outside the int32 fixed-point range are reported by
  * bf_workspace_status (BF_EUNSUPPORTED).
+ * Zero fields: when every h_i is 0, E(c) = E(~c); a search over the whole
+ * space (fixed_bits = 0) of more than 2^20 configurations with the Gray walk
+ * and S <= 1 + n + n(n-1)/2 then enumerates only the configurations with spin
+ * n-1 at -1 and adds the mirrors c ^ (2^n - 1) to the result.  The output is
+ * the same as that of the full enumeration.
  * Streams: the enumeration kernel reads its per-instance step increments from
  * one table per device, which the call fills from the workspace just before
  * the kernel.  Searches queued on different streams are ordered around that
@@ -259,7 +264,9 @@ size_t bf_batched_workspace_size(int B, int n_max, int S, bf_dtype dtype, const 
  * opt->grid_blocks the persistent grid.  No host synchronisation and no
  * allocation: the call is capturable in a CUDA graph.  Instances with n out
  * of range are reported by bf_workspace_status as BF_EINVAL (their output
- * rows are left unwritten).
+ * rows are left unwritten).  Instances with all h_i = 0 and n >= 11 enumerate
+ * only the configurations with spin n-1 at -1 (E(c) = E(~c)); their rows
+ * include the mirrors c ^ (2^n - 1) and equal those of the full enumeration.
  */
 bf_status bf_low_spectrum_batched(int B, const void* J_packed, const int64_t* J_offsets,
                                   const void* h_packed, const int64_t* h_offsets, const int32_t* n,
